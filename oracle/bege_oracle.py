@@ -1,0 +1,234 @@
+"""Plain FP64 CPU oracle of the matched-filter search (van Putten, arXiv:1708.01609).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the product library.
+
+What it computes, in the paper's order (Sec. 3 and Sec. 3.2):
+
+1. Templates (Sec. 3, Eq. s; chirp form of the synthetic bank):
+   w[m] = T(m) sin(2 pi (f0 t_m + fdot t_m^2 / 2)), t_m = m / fs, m < L, with
+   T a cosine (Tukey) taper, scaled to unit L2 norm, zero-padded to N.
+2. Correlation (Eq. A1 discretised, circular):
+   rho[n] = sum_m w[m] y[(n + m) mod N], n = 0..N-1.
+   ``correlate_direct`` writes this sum out; ``correlate_fft`` evaluates it by
+   the three steps of Eq. 3S with this module's own radix-2 FFT:
+   {W, D} = FFT{w, y}; P = conj(W) D; rho = FFT^-1{P}.
+3. sigma (the definition below Eq. 3S, and Eq. PT): RMS of rho about zero,
+   predicted from the spectrum by Parseval's theorem.
+4. Tails (Eq. tail, applied to |rho| as the paper states): every
+   (k, n, rho_k[n]) with |rho_k[n]| > kappa sigma_k ("all hits", Sec. 3.3).
+
+Readings of the paper taken here (the paper is garbled or silent):
+
+* Eq. A1 integrates over "dt"; it must be ds.  The lag convention y(t+s)
+  places a template injected at y[l + m] at lag n = l.
+* Eq. A3 normalises c_k with 1/N, which contradicts the sqrt(2)/N prefactor
+  of Eq. PT.  Eq. PT holds for UNnormalised coefficients P_j = sum_n rho_n
+  e^{-2 pi i j n / N}; then sigma^2 = (1/N^2) sum_{j<N} |P_j|^2
+  = (1/N^2)(|P_0|^2 + |P_{N/2}|^2 + 2 sum_{j=1}^{N/2-1} |P_j|^2).  The printed
+  form drops DC and Nyquist; ``sigma_parseval_paper_form`` keeps that form and
+  equals ``sigma_parseval`` when those two bins vanish.
+* The forward transform uses e^{-i k t} (Eq. A2), the inverse e^{+...}/N.
+* The threshold is strict: |rho| > kappa sigma (Eq. tail writes ">").
+* The correlation is circular over all N lags (the template is zero-padded to
+  N, Sec. 3.2 step ii, and transformed with an N-point FFT).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+TAIL_DTYPE = np.dtype([("tmpl", np.uint32), ("lag", np.uint32), ("value", np.float64)])
+
+
+# ----------------------------------------------------------------------------
+# FFT (Eq. 3S, with the sign convention of Eq. A2)
+# ----------------------------------------------------------------------------
+def _bit_reverse(n: int) -> np.ndarray:
+    bits = n.bit_length() - 1
+    idx = np.arange(n)
+    rev = np.zeros(n, dtype=np.int64)
+    for b in range(bits):
+        rev |= ((idx >> b) & 1) << (bits - 1 - b)
+    return rev
+
+
+def fft(x: np.ndarray, inverse: bool = False) -> np.ndarray:
+    """Unnormalised radix-2 Cooley-Tukey FFT over the last axis, FP64.
+
+    Forward: X_j = sum_n x_n exp(-2 pi i j n / N)   (sign of Eq. A2)
+    Inverse: x_n = sum_j X_j exp(+2 pi i j n / N)   (no 1/N here)
+
+    Textbook decimation in time: bit-reversal permutation, then log2(N)
+    stages of size-2 butterflies, each stage vectorised over the batch.
+    """
+    a = np.asarray(x, dtype=np.complex128)
+    n = a.shape[-1]
+    if n & (n - 1) or n == 0:
+        raise ValueError("FFT length must be a power of two")
+    lead = a.shape[:-1]
+    a = a[..., _bit_reverse(n)].copy()
+    sign = 1.0 if inverse else -1.0
+    size = 2
+    while size <= n:
+        half = size // 2
+        tw = np.exp(sign * 2j * np.pi * np.arange(half) / size)
+        blocks = a.reshape(*lead, n // size, size)
+        even = blocks[..., :half]
+        odd = blocks[..., half:] * tw
+        a = np.concatenate([even + odd, even - odd], axis=-1).reshape(*lead, n)
+        size *= 2
+    return a
+
+
+# ----------------------------------------------------------------------------
+# Templates (Sec. 3, Eq. s: chirps over a range of f and fdot)
+# ----------------------------------------------------------------------------
+def taper(length: int, frac: float) -> np.ndarray:
+    """Cosine taper: 0.5(1 - cos(2 pi m / (frac (L-1)))) on the first
+    floor(frac (L-1) / 2) + 1 samples, mirrored at the end, 1 in between."""
+    t = np.ones(length, dtype=np.float64)
+    if frac <= 0.0 or length < 2:
+        return t
+    width = int(math.floor(frac * (length - 1) / 2.0))
+    for m in range(width + 1):
+        v = 0.5 * (1.0 - math.cos(2.0 * math.pi * m / (frac * (length - 1))))
+        t[m] = v
+        t[length - 1 - m] = v
+    return t
+
+
+def chirp_template(f0: float, fdot: float, fs: float, length: int,
+                   taper_frac: float) -> np.ndarray:
+    """Unit-norm tapered linear chirp, FP64, length ``length``."""
+    t = np.arange(length, dtype=np.float64) / fs
+    w = taper(length, taper_frac) * np.sin(2.0 * np.pi * (f0 * t + 0.5 * fdot * t * t))
+    return w / math.sqrt(float(np.dot(w, w)))
+
+
+def chirp_bank(params: np.ndarray, fs: float, length: int, taper_frac: float) -> np.ndarray:
+    """Templates for rows (f0, fdot) of ``params``; shape (K, length), FP64."""
+    return np.stack([chirp_template(f0, fd, fs, length, taper_frac) for f0, fd in params])
+
+
+# ----------------------------------------------------------------------------
+# Correlation (Eq. A1, Eq. 3S)
+# ----------------------------------------------------------------------------
+def correlate_direct(w: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Eq. A1 as a finite circular sum: rho[n] = sum_m w[m] y[(n+m) mod N]."""
+    w = np.asarray(w, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n = len(y)
+    rho = np.zeros(n)
+    for m in range(len(w)):
+        rho += w[m] * np.roll(y, -m)   # np.roll(y, -m)[n] = y[(n+m) mod N]
+    return rho
+
+
+def zero_pad(w: np.ndarray, n: int) -> np.ndarray:
+    w = np.asarray(w, dtype=np.float64)
+    if w.shape[-1] > n:
+        raise ValueError("template longer than segment")
+    out = np.zeros(w.shape[:-1] + (n,))
+    out[..., : w.shape[-1]] = w
+    return out
+
+
+def correlation_spectrum(w: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Eq. 3S steps 1-2: P = conj(FFT w) * FFT y (w zero-padded to N)."""
+    n = len(y)
+    big_w = fft(zero_pad(w, n))
+    big_d = fft(np.asarray(y, dtype=np.float64))
+    return np.conj(big_w) * big_d
+
+
+def correlate_fft(w: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Eq. 3S: rho = FFT^-1{conj(W) D}; returns the real part (the imaginary
+    part is rounding noise because rho is real)."""
+    p = correlation_spectrum(w, y)
+    n = p.shape[-1]
+    return (fft(p, inverse=True) / n).real
+
+
+# ----------------------------------------------------------------------------
+# sigma (definition below Eq. 3S; Eq. PT)
+# ----------------------------------------------------------------------------
+def sigma_rms(rho: np.ndarray) -> np.ndarray:
+    """sigma = (1/sqrt N) sqrt(sum_n rho_n^2): the RMS of rho about zero."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return np.sqrt(np.sum(rho * rho, axis=-1) / rho.shape[-1])
+
+
+def sigma_parseval(p: np.ndarray) -> np.ndarray:
+    """Eq. PT with unnormalised coefficients of rho (reading in module doc):
+    sigma = (1/N) sqrt(sum_{j=0}^{N/2} c_j |P_j|^2), c_0 = c_{N/2} = 1, else 2."""
+    p = np.asarray(p)
+    n = p.shape[-1]
+    h = n // 2
+    mag2 = (p[..., : h + 1] * np.conj(p[..., : h + 1])).real
+    c = np.full(h + 1, 2.0)
+    c[0] = 1.0
+    c[h] = 1.0
+    return np.sqrt(np.sum(c * mag2, axis=-1)) / n
+
+
+def sigma_parseval_paper_form(p: np.ndarray) -> np.ndarray:
+    """Eq. PT as printed: (sqrt 2 / N) sqrt(sum_{j=1}^{N/2-1} |P_j|^2)."""
+    p = np.asarray(p)
+    n = p.shape[-1]
+    h = n // 2
+    mag2 = (p[..., 1:h] * np.conj(p[..., 1:h])).real
+    return math.sqrt(2.0) * np.sqrt(np.sum(mag2, axis=-1)) / n
+
+
+# ----------------------------------------------------------------------------
+# Tails (Eq. tail, all hits)
+# ----------------------------------------------------------------------------
+def tails(rho: np.ndarray, sigma: float, kappa: float, k: int) -> np.ndarray:
+    """All (k, n, rho[n]) with |rho[n]| > kappa * sigma, ordered by n."""
+    rho = np.asarray(rho, dtype=np.float64)
+    lags = np.nonzero(np.abs(rho) > kappa * sigma)[0]
+    out = np.empty(len(lags), dtype=TAIL_DTYPE)
+    out["tmpl"] = k
+    out["lag"] = lags
+    out["value"] = rho[lags]
+    return out
+
+
+def search(y: np.ndarray, templates: np.ndarray, kappa: float, k0: int = 0,
+           batch: int = 32, return_rho: bool = False) -> dict:
+    """Correlate segment ``y`` with every template row and keep the tails.
+
+    Returns {"tails": TAIL_DTYPE array sorted by (tmpl, lag), "sigma": (K,),
+    "rho": (K, N) if requested}.  Template index = k0 + row.
+    """
+    y = np.asarray(y, dtype=np.float64)
+    n = len(y)
+    templates = np.atleast_2d(np.asarray(templates, dtype=np.float64))
+    big_d = fft(y)
+    sig = np.empty(len(templates))
+    recs = []
+    rhos = np.empty((len(templates), n)) if return_rho else None
+    for s in range(0, len(templates), batch):
+        w = templates[s:s + batch]
+        p = np.conj(fft(zero_pad(w, n))) * big_d
+        rho = (fft(p, inverse=True) / n).real
+        sg = sigma_parseval(p)
+        sig[s:s + len(w)] = sg
+        for r in range(len(w)):
+            recs.append(tails(rho[r], sg[r], kappa, k0 + s + r))
+        if return_rho:
+            rhos[s:s + len(w)] = rho
+    t = np.concatenate(recs) if recs else np.empty(0, dtype=TAIL_DTYPE)
+    t = np.sort(t, order=["tmpl", "lag"])
+    out = {"tails": t, "sigma": sig}
+    if return_rho:
+        out["rho"] = rhos
+    return out
+
+
+def near_threshold(values: np.ndarray, sigma: np.ndarray, kappa: float,
+                   band: float = 1e-3) -> np.ndarray:
+    """True where ||rho| - kappa sigma| <= band * sigma (excluded from set parity)."""
+    return np.abs(np.abs(values) - kappa * sigma) <= band * sigma

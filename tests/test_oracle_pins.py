@@ -1,0 +1,314 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test names the passage it checks.  Chosen so that a plausible slip in the
+oracle (a sign, a dropped term, a conjugate, an off-by-one in lags, a wrong
+Parseval weight, >= for >) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# --------------------------------------------------------------------------
+# FFT (Eq. 3S, sign of Eq. A2)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 64, 1024, 4096])
+def test_fft_matches_library(n):
+    """Library special case: numpy.fft uses the same e^{-i...} forward kernel."""
+    r = rng(n)
+    x = r.standard_normal((3, n)) + 1j * r.standard_normal((3, n))
+    got = O.fft(x)
+    ref = np.fft.fft(x, axis=-1)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+    inv = O.fft(x, inverse=True)
+    ref_inv = np.fft.ifft(x, axis=-1) * n
+    assert np.max(np.abs(inv - ref_inv)) <= 1e-12 * max(1.0, np.max(np.abs(ref_inv)))
+
+
+def test_fft_closed_forms():
+    """Closed forms: a delta transforms to ones; exp(+2 pi i q n/N) transforms
+    to N at bin q under the forward kernel exp(-2 pi i j n / N) (Eq. A2)."""
+    n = 256
+    d = np.zeros(n)
+    d[0] = 1.0
+    assert np.allclose(O.fft(d), np.ones(n), atol=1e-14)
+    q = 37
+    x = np.exp(2j * np.pi * q * np.arange(n) / n)
+    X = O.fft(x)
+    expect = np.zeros(n, complex)
+    expect[q] = n
+    assert np.max(np.abs(X - expect)) < 1e-10
+    # round trip with the 1/N of the inverse
+    r = rng(5).standard_normal(n)
+    assert np.max(np.abs(O.fft(O.fft(r), inverse=True) / n - r)) < 1e-13
+
+
+def test_fft_rejects_non_power_of_two():
+    with pytest.raises(ValueError):
+        O.fft(np.zeros(12))
+
+
+# --------------------------------------------------------------------------
+# Correlation (Eq. A1, Eq. 3S)
+# --------------------------------------------------------------------------
+def test_cosine_closed_form():
+    """Eq. A1 against a closed form: y[n] = cos(th n), w[m] = cos(th m), m < L
+    gives rho[n] = (L/2) cos(th n) + (1/2) Re[e^{i th n} (1 - e^{2 i th L}) /
+    (1 - e^{2 i th})] (sum of a geometric series)."""
+    n, length, q = 128, 21, 5
+    th = 2 * np.pi * q / n
+    y = np.cos(th * np.arange(n))
+    w = np.cos(th * np.arange(length))
+    nn = np.arange(n)
+    geo = (1 - np.exp(2j * th * length)) / (1 - np.exp(2j * th))
+    expect = 0.5 * length * np.cos(th * nn) + 0.5 * (np.exp(1j * th * nn) * geo).real
+    assert np.max(np.abs(O.correlate_direct(w, y) - expect)) < 1e-12
+    assert np.max(np.abs(O.correlate_fft(w, y) - expect)) < 1e-11
+
+
+@pytest.mark.parametrize("n,length", [(16, 5), (256, 100), (1024, 1024), (1024, 7)])
+def test_fft_correlation_equals_direct(n, length):
+    """Eq. 3S reproduces Eq. A1 (brute force on small inputs)."""
+    r = rng(n + length)
+    y = r.standard_normal(n)
+    w = r.standard_normal(length)
+    a = O.correlate_direct(w, y)
+    b = O.correlate_fft(w, y)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a)) * math.log2(n)
+
+
+@pytest.mark.parametrize("lag", [0, 1, 300, 1023])
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_injection_recovered_at_lag_and_amplitude(lag, sign):
+    """Lag convention y(t+s): a unit-norm template placed at y[l + m] gives
+    rho[l] = A exactly, and |rho| peaks there (Cauchy-Schwarz).  Also covers a
+    wrap past the end of the segment (circular correlation)."""
+    n, length = 1024, 200
+    w = rng(3).standard_normal(length)
+    w /= np.linalg.norm(w)
+    y = np.zeros(n)
+    a = 7.25 * sign
+    y[(lag + np.arange(length)) % n] += a * w
+    rho = O.correlate_fft(w, y)
+    assert abs(rho[lag] - a) < 1e-12
+    assert int(np.argmax(np.abs(rho))) == lag
+
+
+def test_self_correlation_is_one():
+    """A unit-norm chirp template against itself (zero-padded) gives rho[0] = 1."""
+    w = O.chirp_template(1000.0, 50.0, 4096.0, 4096, 0.05)
+    y = O.zero_pad(w, 1 << 14)
+    rho = O.correlate_fft(w, y)
+    assert abs(rho[0] - 1.0) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# sigma (definition below Eq. 3S; Eq. PT)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [16, 1024, 4096])
+def test_parseval_identity(n):
+    """Parseval: the spectral sigma equals the RMS of rho, including data with
+    non-zero DC and Nyquist (all Parseval weights matter)."""
+    r = rng(n)
+    y = r.standard_normal(n) + 0.3          # non-zero mean -> DC bin
+    y[::2] += 0.2                            # Nyquist content
+    w = r.standard_normal(min(n, 300))
+    p = O.correlation_spectrum(w, y)
+    rho = (O.fft(p, inverse=True) / n).real
+    assert abs(O.sigma_parseval(p) / O.sigma_rms(rho) - 1.0) < 1e-12
+
+
+def test_paper_form_needs_vanishing_dc_and_nyquist():
+    """Eq. PT as printed equals the full form when DC and Nyquist vanish
+    (band-limited data), and differs when they do not."""
+    n = 4096
+    y = S.band_limited_noise(n, 11).astype(np.float64)
+    y -= 0.0
+    w = O.chirp_template(900.0, -30.0, 4096.0, 2048, 0.05)
+    p = O.correlation_spectrum(w, y)
+    p[0] = 0.0
+    p[n // 2] = 0.0
+    assert abs(O.sigma_parseval(p) / O.sigma_parseval_paper_form(p) - 1) < 1e-13
+    p2 = p.copy()
+    p2[0] = 50.0 * np.abs(p).max()
+    assert O.sigma_parseval(p2) > 1.01 * O.sigma_parseval_paper_form(p2)
+
+
+@pytest.mark.slow
+def test_sigma_matches_ensemble_prediction():
+    """On band-limited Gaussian noise the Parseval sigma matches the ensemble
+    prediction sigma_E^2 = (s^2/N^2) sum_{in band} 2|W_j|^2 within sampling
+    error (200 seeds, 4 standard errors)."""
+    n = 4096
+    w = O.chirp_template(800.0, 40.0, 4096.0, 2048, 0.05)
+    big_w = np.fft.rfft(O.zero_pad(w, n))
+    jb = S.band_bins(n)
+    s = S.noise_scale(n)
+    sig_e2 = (s * s / n / n) * 2.0 * np.sum(np.abs(big_w[jb]) ** 2)
+    ratios = []
+    for seed in range(200):
+        y = S.band_limited_noise(n, 1000 + seed)
+        ratios.append(O.sigma_parseval(O.correlation_spectrum(w, y)) ** 2 / sig_e2)
+    ratios = np.array(ratios)
+    se = ratios.std(ddof=1) / math.sqrt(len(ratios))
+    assert abs(ratios.mean() - 1.0) < 4 * se
+
+
+# --------------------------------------------------------------------------
+# Tails (Eq. tail)
+# --------------------------------------------------------------------------
+def test_tails_strict_and_absolute():
+    """|rho| > kappa sigma, strict, on the absolute value (text under Eq. tail)."""
+    rho = np.array([0.0, 5.0, -5.0, 5.0000001, -6.0, 4.9])
+    t = O.tails(rho, 1.0, 5.0, 9)
+    assert t["lag"].tolist() == [3, 4]
+    assert t["tmpl"].tolist() == [9, 9]
+    assert t["value"].tolist() == [5.0000001, -6.0]
+
+
+@pytest.mark.slow
+def test_noise_tail_rate_is_gaussian():
+    """For Gaussian noise the rate of |rho| > kappa sigma is 2 Q(kappa).
+
+    Broadband templates keep the filter output's degrees of freedom high
+    (~2 x 1650 Hz x 1 s); a narrowband chirp on a 1 s segment has so few that
+    the realised sigma tracks its own peaks and the rate falls below 2 Q."""
+    n, kappa = 4096, 3.0
+    bank = rng(8).standard_normal((8, 1024))
+    counts = []
+    for seed in range(40):
+        y = S.band_limited_noise(n, 500 + seed)
+        counts.append(len(O.search(y, bank, kappa)["tails"]))
+    counts = np.array(counts, float)
+    expect = math.erfc(kappa / math.sqrt(2)) * n * len(bank)
+    se = counts.std(ddof=1) / math.sqrt(len(counts))
+    assert abs(counts.mean() - expect) < 4 * se + 0.02 * expect
+
+
+def test_search_matches_per_template_definition():
+    """search() batches, offsets template indices and sorts; compare it with
+    the direct definition applied template by template (batch 3 over 7)."""
+    n = 256
+    r = rng(77)
+    y = r.standard_normal(n)
+    bank = r.standard_normal((7, 40))
+    kappa = 2.0
+    got = O.search(y, bank, kappa, k0=100, batch=3, return_rho=True)
+    recs = []
+    for i, w in enumerate(bank):
+        rho = O.correlate_direct(w, y)
+        sg = O.sigma_rms(rho)
+        assert abs(got["sigma"][i] / sg - 1) < 1e-12
+        assert np.max(np.abs(got["rho"][i] - rho)) < 1e-11
+        recs.append(O.tails(rho, sg, kappa, 100 + i))
+    ref = np.concatenate(recs)
+    assert got["tails"]["tmpl"].tolist() == ref["tmpl"].tolist()
+    assert got["tails"]["lag"].tolist() == ref["lag"].tolist()
+    assert np.allclose(got["tails"]["value"], ref["value"], rtol=0, atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# Templates (Sec. 3 chirps)
+# --------------------------------------------------------------------------
+def test_taper_matches_library():
+    """Library special case: scipy's Tukey window with the same fraction."""
+    sw = pytest.importorskip("scipy.signal.windows")
+    for length, frac in [(4096, 0.05), (2048, 0.05), (101, 0.3), (11, 0.5)]:
+        assert np.max(np.abs(O.taper(length, frac) - sw.tukey(length, frac))) < 1e-14
+
+
+def test_chirp_template_closed_form():
+    """Scalar evaluation of T(m) sin(2 pi (f0 t + fdot t^2/2)) with math.sin at
+    a few samples of the untapered middle; the template is that times 1/norm."""
+    f0, fd, fs, length = 1234.5, -87.25, 4096.0, 4096
+    w = O.chirp_template(f0, fd, fs, length, 0.05)
+    raw = [math.sin(2 * math.pi * (f0 * (m / fs) + 0.5 * fd * (m / fs) ** 2))
+           for m in range(length)]
+    tap = O.taper(length, 0.05)
+    norm = math.sqrt(sum((tap[m] * raw[m]) ** 2 for m in range(length)))
+    for m in [0, 1, 57, 102, 103, 2000, 3333, 4095]:
+        assert abs(w[m] - tap[m] * raw[m] / norm) < 1e-15
+    assert abs(np.dot(w, w) - 1.0) < 1e-13
+
+
+def test_injected_signal_matches_template():
+    """The generator's injected chirp (independent code) equals the oracle's
+    template: a noise-free injection of amplitude A reads rho = A at its lag."""
+    params = S.grid_small()
+    k = 27
+    f0, fd = params[k]
+    n = 1 << 14
+    sig = S.chirp_signal(f0, fd, 4096)
+    y = np.zeros(n)
+    y[(5000 + np.arange(4096)) % n] = 3.5 * sig
+    w = O.chirp_template(f0, fd, 4096.0, 4096, 0.05)
+    rho = O.correlate_fft(w, y)
+    assert abs(rho[5000] - 3.5) < 1e-12
+
+
+def test_chirp_spectrum_inside_band():
+    """Every chirp of the paper-scale grid sweeps inside 350-2000 Hz: its
+    spectral energy more than 50 Hz outside the band (taper and 1 s
+    time-limiting leakage only) is tiny."""
+    params = S.grid_paper(8, 8)
+    n = 1 << 16
+    f = np.arange(n // 2 + 1) * 4096.0 / n
+    out_band = (f < 300) | (f > 2050)
+    for f0, fd in params:
+        w = O.chirp_template(f0, fd, 4096.0, 4096, 0.05)
+        p = np.abs(np.fft.rfft(O.zero_pad(w, n))) ** 2
+        assert p[out_band].sum() / p.sum() < 1e-4
+
+
+# --------------------------------------------------------------------------
+# Recovery and the time-randomisation null (Sec. 5)
+# --------------------------------------------------------------------------
+def test_small_case_recovers_injection():
+    """The N=2^14 parity case: the 20-sigma injection of template 27 at lag
+    5000 is a tail of template 27 at lag 5000 with |rho - A| <= 4 sigma."""
+    seg, params = S.small_case()
+    bank = O.chirp_bank(params, 4096.0, 4096, 0.05)
+    res = O.search(seg.y, bank, 5.0)
+    k, lag, a = seg.injections[0]
+    t = res["tails"]
+    hit = t[(t["tmpl"] == k) & (t["lag"] == lag)]
+    assert len(hit) == 1
+    assert abs(hit["value"][0] - a) <= 4 * res["sigma"][k]
+
+
+def test_time_randomised_null():
+    """Time-randomising the injected segment (Sec. 5) removes the injection's
+    coherent peak: before, |rho|/sigma > 8 at the injection (the injection's
+    own power raises the Parseval sigma above the noise-only value); after,
+    the largest |rho|/sigma over the bank is Gaussian-like (< 6.5)."""
+    seg, params = S.small_case()
+    bank = O.chirp_bank(params, 4096.0, 4096, 0.05)
+    k, lag, a = seg.injections[0]
+    before = O.search(seg.y, bank[k:k + 1], 5.0, return_rho=True)
+    assert abs(before["rho"][0][lag]) / before["sigma"][0] > 8
+    y2 = rng(4).permutation(seg.y)
+    after = O.search(y2, bank, 5.0, return_rho=True)
+    z = np.max(np.abs(after["rho"]), axis=1) / after["sigma"]
+    assert z.max() < 6.5
+
+
+# --------------------------------------------------------------------------
+# The synthetic noise recipe
+# --------------------------------------------------------------------------
+def test_noise_recipe():
+    """Unit variance in expectation and no power outside the band."""
+    n = 1 << 14
+    ys = np.stack([S.band_limited_noise(n, s) for s in range(20)]).astype(np.float64)
+    assert abs(np.mean(ys * ys) - 1.0) < 0.02
+    spec = np.abs(np.fft.rfft(ys[0])) ** 2
+    f = np.arange(n // 2 + 1) * 4096.0 / n
+    outside = (f < 350) | (f > 2000)
+    assert spec[outside].sum() < 1e-9 * spec.sum()
