@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Throughput of the FFT matched-filter search of arXiv:1708.01609 on GB300.
+
+One step is one pass of the whole hot path over one synthetic segment:
+  S1     segment spectrum of an N = 2^16 strain segment resident in HBM,
+  S2-S6  the fused correlate kernel over all 2^20 chirp templates (template
+         spectrum, spectral product, Parseval sigma, inverse FFT, kappa-sigma
+         threshold, tail compaction), kappa = 5.5,
+  S7     fetch of the tail count and records to host memory.
+The metric is chirp correlations per second (templates x segments / s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 it runs under torch.distributed.run, one rank per GPU, each rank
+searching its own segment against the full bank (weak scaling; no collective
+on the data path, only the barrier and the max-over-ranks time).  Rank 0
+prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+from paper_1708_01609_gb300 import metrics  # noqa: E402
+
+N_SAMPLES = 1 << 16
+KAPPA = 5.5
+METRIC = "chirp correlations/s at N=2^16"
+UNIT = "correlations/s"
+
+
+def workload_config(templates: int, world: int) -> dict:
+    return {
+        "workload": (f"N=2^16 band-limited (350-2000 Hz) strain segment x {templates} chirp "
+                     "templates (1024 f0 x 1024 fdot grid, tau 1 s, 5% taper), kappa 5.5, "
+                     "32 injections SNR 8-30"),
+        "segment_len": N_SAMPLES,
+        "templates": templates,
+        "kappa": KAPPA,
+        "fs_hz": 4096.0,
+        "l2": "inputs larger than L2: the 17.2 GB FP32 bank is streamed from HBM every step",
+        "parallelism": f"{world} independent replica(s), one segment per GPU per step",
+    }
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands
+# ---------------------------------------------------------------------------
+def oracle_sample(seconds: float, max_templates: int, batch: int = 8):
+    """Time the oracle on the first templates of the benchmark bank until
+    ``seconds`` of CPU work or ``max_templates`` are done."""
+    import oracle as O
+    seg, params = S.paper_case()
+    y = seg.y
+    done = 0
+    t0 = time.perf_counter()
+    while done < max_templates:
+        bank = O.chirp_bank(params[done:done + batch], 4096.0, 4096, 0.05)
+        O.search(y, bank, KAPPA, k0=done, batch=batch)
+        done += len(bank)
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt
+
+
+def cpu_baseline(seconds: float = 15.0) -> dict:
+    done, dt = oracle_sample(seconds, 4096)
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle (own radix-2 FFT, numpy, one process) on the first {done} "
+                       f"templates of the 2^20 bank against the N=2^16 segment, {dt:.1f} s")}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle timed as the reference implementation
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    per_step = args.ref_templates
+    for _ in range(args.warmup):
+        oracle_sample(0.0, per_step, batch=per_step)
+    times = []
+    for _ in range(args.steps):
+        done, dt = oracle_sample(0.0, per_step, batch=per_step)
+        times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(1 << 20, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": (f"each step: FP64 oracle on {per_step} templates of the "
+                                    "2^20 bank against the N=2^16 segment, one process")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def traffic_record(templates: int):
+    """DRAM bytes per correlate launch from the committed ncu summary, if the
+    kernel source is unchanged since it was captured; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get("correlate_kernel")
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1708_01609_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(src)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(src, name), "rb").read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec["dram_bytes_per_correlation"] * templates
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1708_01609_gb300 import binding, build
+    build()
+    cap = 1 << 25   # all hits of 32 strong injections per segment run to ~1.4e7 records
+    ctx = binding.Context(local, tail_capacity=cap)
+    templates = args.templates
+    seg_data, params = S.paper_case(seed=2017 + rank)
+    params = params[:templates]
+    stream_obj = torch.cuda.current_stream()
+    stream = stream_obj.cuda_stream
+    bank = ctx.bege_define_bank(params, tau=1.0, taper_frac=0.05, stream=stream)
+    y_dev = torch.from_numpy(seg_data.y).cuda()
+    y_pin = torch.from_numpy(seg_data.y).pin_memory()
+    y_host = y_pin.numpy()
+    out = torch.empty(cap * 12, dtype=torch.uint8).pin_memory().numpy().view(binding.TAIL_DTYPE)
+    torch.cuda.synchronize()
+
+    def step(host: bool):
+        if host:
+            seg = ctx.bege_load_segment(y_host, 0, stream)
+        else:
+            seg = ctx.bege_load_segment_device(y_dev.data_ptr(), N_SAMPLES, 0, stream)
+        job = ctx.bege_correlate(seg, bank, 0, templates, KAPPA, stream)
+        recs, total = ctx.bege_fetch_tails(job, out=out)
+        if len(recs) != total:
+            raise RuntimeError(f"tail buffer overflow: {total} tails, {len(recs)} copied")
+        kms = ctx.bege_job_kernel_ms(job)
+        ctx.bege_release(job)
+        ctx.bege_release(seg)
+        return total, kms
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(host: bool, steps: int, clocks: ClockSampler | None = None):
+        barrier()
+        if clocks:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream_obj)
+        tails, kms = [], []
+        for _ in range(steps):
+            t, k = step(host)
+            tails.append(t)
+            kms.append(k)
+        e1.record(stream_obj)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, tails, kms, clk
+
+    for _ in range(args.warmup):
+        step(False)
+    ms, tails, kms, clk = timed(False, args.steps, ClockSampler(local))
+    for _ in range(max(1, args.warmup // 2)):
+        step(True)
+    ms_e2e, tails_e2e, _, _ = timed(True, args.steps)
+
+    units = templates * world * args.steps
+    value = units / (ms / 1e3)
+    value_e2e = units / (ms_e2e / 1e3)
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz") or 2070.0
+    peak = metrics.fp32_peak_flops(props.multi_processor_count, sm_max)
+    kernel_ms = statistics.mean(kms)
+    flops_launch = templates * metrics.nominal_flops_per_correlation(N_SAMPLES)
+    achieved = flops_launch / (kernel_ms / 1e3)
+    traffic = traffic_record(templates)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(templates, world),
+        "roofline": {
+            "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": "correlate_kernel<4096,4>", "kernel_ms": kernel_ms,
+            "flops_per_launch": flops_launch,
+            "peak_basis": (f"FP32 ALU: {props.multi_processor_count} SMs x 128 lanes x 2 flops x "
+                           f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)"),
+            "flop_convention": "5 N log2 N per correlation (Eq. nd)",
+        },
+        "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": N_SAMPLES * 4,
+                "d2h_bytes_per_step": int(8 + 12 * statistics.mean(tails_e2e))},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "tails_per_step": statistics.mean(tails),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--templates", type=int, default=1 << 20,
+                    help="bank rows per step (the benchmark uses all 2^20)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-templates", type=int, default=8,
+                    help="templates per reference-arm step (bounded oracle sample)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * bege.h -- C ABI of libbege, the GPU matched-filter search for broadband
+ * extended gravitational-wave emission (van Putten, arXiv:1708.01609).
+ *
+ * The library computes, for one strain segment y of N samples and a bank of
+ * real templates w_k of L <= N samples (zero-padded to N), the circular
+ * correlation of Eq. A1 through the three FFT steps of Eq. 3S,
+ *     rho_k[n] = sum_{m<L} w_k[m] y[(n+m) mod N],   n = 0..N-1,
+ * predicts sigma_k = sqrt((1/N) sum_n rho_k[n]^2) from the spectra by
+ * Parseval's theorem (Eq. PT, read with unnormalised Fourier coefficients),
+ * and returns only the tails |rho_k[n]| > kappa sigma_k (Eq. tail, the
+ * "all hits" output of Sec. 3.3) as (template, lag, value) records.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a bege_status (0 = BEGE_OK, negative = error).  On
+ *     error, bege_last_error() gives a message for the calling thread.
+ *   - Handles (segments, banks, jobs) are int32 ids owned by the context.
+ *     The library owns all device memory it allocates; the caller owns every
+ *     host buffer it passes and may reuse it as soon as the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream only enqueue work on it; the calls
+ *     that return results to host memory synchronise on the job themselves.
+ *   - Lags are circular indices 0..N-1.  Template indices are bank rows.
+ *   - Sizes: N is a power of two in [2^10, 2^17]; 1 <= L <= min(N, 2^16).
+ *   - Device: one context drives one GPU (sm_103a).  No CPU fallback exists:
+ *     if no usable GPU is present bege_create fails with BEGE_ECUDA.
+ */
+#ifndef BEGE_H
+#define BEGE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bege_ctx bege_ctx; /* opaque, library-owned */
+
+typedef enum {
+  BEGE_OK = 0,
+  BEGE_EINVAL = -1,      /* malformed argument or unknown handle            */
+  BEGE_ENOMEM = -2,      /* device or host allocation failed                */
+  BEGE_EBUDGET = -3,     /* request would exceed hbm_budget_bytes           */
+  BEGE_EOVERFLOW = -4,   /* more tails than the buffers hold; count is true */
+  BEGE_ENOTREADY = -5,   /* job not finished (non-blocking query)           */
+  BEGE_ETIMEDOUT = -6,   /* a bounded device wait gave up                   */
+  BEGE_ECUDA = -7        /* CUDA runtime error (message in last_error)      */
+} bege_status;
+
+typedef struct {
+  double fs;                  /* sample rate in Hz (the paper: 4096, Sec. 3)     */
+  uint64_t hbm_budget_bytes;  /* cap on library-owned device memory; 0 = none    */
+  uint64_t tail_capacity;     /* device tail records per job; 0 = 1<<20          */
+  int32_t precision;          /* 0 = FP32 (the only value accepted for now)      */
+  int32_t reserved;           /* must be 0                                       */
+} bege_config;
+
+/* Linear chirp f(t) = f0 + fdot t (Sec. 3, Eq. s bank over (f, fdot)). */
+typedef struct {
+  double f0;    /* Hz   */
+  double fdot;  /* Hz/s */
+} bege_chirp;
+
+/* One tail record (Eq. tail, all hits): template row, lag n, signed rho. */
+typedef struct {
+  uint32_t tmpl;
+  uint32_t lag;
+  float value;
+} bege_tail;
+
+/* Create a context on CUDA device `device`.  `cfg` may be NULL for defaults
+ * (fs = 4096, no budget, 1<<20 tail records, FP32).  *out receives the
+ * context; destroy it with bege_destroy.  Errors: EINVAL (bad cfg), ECUDA. */
+int bege_create(bege_ctx** out, int device, const bege_config* cfg);
+
+/* Free every device buffer and handle of the context. */
+int bege_destroy(bege_ctx* ctx);
+
+/* Segment spectrum (Eq. 3S first step; Sec. 3.2 step i).  Copies `n` FP32
+ * strain samples from HOST memory `strain`, computes the unnormalised DFT
+ * D_j = sum_n y[n] e^{-2 pi i j n / N}, j = 0..N/2, and keeps it resident on
+ * the device (with the derived product coefficients used by bege_correlate).
+ * `channel` is a caller label (e.g. 0 = H1, 1 = L1) stored with the segment.
+ * *seg_id receives the handle.  Errors: EINVAL (n not a power of two in
+ * range, NULL pointers), EBUDGET, ENOMEM, ECUDA. */
+int bege_load_segment(bege_ctx* ctx, const float* strain, int64_t n, int32_t channel,
+                      void* stream, int32_t* seg_id);
+
+/* As bege_load_segment, but `strain_dev` is a DEVICE pointer to n FP32
+ * samples on the context's GPU (read on `stream`; not retained). */
+int bege_load_segment_device(bege_ctx* ctx, const float* strain_dev, int64_t n,
+                             int32_t channel, void* stream, int32_t* seg_id);
+
+/* Template bank from chirp parameters (Sec. 3: one-second chirps over the
+ * (f, fdot) plane).  Row k is
+ *     w_k[m] = T(m) sin(2 pi (f0 t_m + fdot t_m^2 / 2)),  t_m = m / fs,
+ * m < L = round(tau fs), T a cosine taper over the fraction `taper_frac`
+ * (half at each end), scaled to unit L2 norm; synthesised on the device with
+ * an exact fixed-point phase and FP64 sin/taper/norm, stored as FP32.
+ * `params` is a HOST array of `count` chirps.  Errors: EINVAL, EBUDGET,
+ * ENOMEM, ECUDA. */
+int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, double tau,
+                     double taper_frac, void* stream, int32_t* bank_id);
+
+/* Template bank from explicit samples: `samples` is a HOST array of
+ * count x length FP32 values, row-major, used as given (no normalisation). */
+int bege_define_bank_samples(bege_ctx* ctx, const float* samples, int64_t count,
+                             int64_t length, void* stream, int32_t* bank_id);
+
+/* Correlate segment `seg_id` with bank rows [k_begin, k_end) and keep the
+ * tails |rho_k[n]| > kappa sigma_k (Eq. 3S, Eq. PT, Eq. tail).  Asynchronous:
+ * enqueues the work on `stream` and returns a job handle at once.  The bank's
+ * L must not exceed the segment's N.  kappa must be finite and >= 0.
+ * Errors: EINVAL, EBUDGET, ENOMEM, ECUDA. */
+int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                   int64_t k_end, float kappa, void* stream, int32_t* job_id);
+
+/* Wait for job `job_id` and copy its tail records to HOST `out` (capacity
+ * records).  *n_total receives the true number of tails; *n_written the
+ * number copied = min(n_total, capacity, device tail capacity).  Records are
+ * in device completion order (not sorted).  Returns BEGE_EOVERFLOW (with the
+ * counts filled in) when n_total exceeds what was copied. */
+int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capacity,
+                     int64_t* n_written, int64_t* n_total);
+
+/* Wait for job `job_id` and report the device time in milliseconds of its
+ * correlate kernel alone (CUDA events recorded on the job's stream right
+ * before and after the launch).  Used for roofline accounting. */
+int bege_job_kernel_ms(bege_ctx* ctx, int32_t job_id, float* ms);
+
+/* Non-blocking: BEGE_OK if the job has finished, BEGE_ENOTREADY if not. */
+int bege_query(bege_ctx* ctx, int32_t job_id);
+
+/* Wait for job `job_id` and copy sigma_k (Eq. PT) for its rows to HOST `out`;
+ * `count` must equal k_end - k_begin of the job. */
+int bege_get_sigma(bege_ctx* ctx, int32_t job_id, float* out, int64_t count);
+
+/* Debug: the full correlation rho_k[0..N-1] for rows [k_begin, k_end) into
+ * HOST `out` ((k_end - k_begin) x N floats, row-major).  Same kernel as
+ * bege_correlate; synchronous on `stream`. */
+int bege_dump_correlation(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                          int64_t k_end, float* out, void* stream);
+
+/* Debug: the segment spectrum D_j, j = 0..N/2, as interleaved (re, im) FP32
+ * into HOST `out` (N + 2 floats). */
+int bege_get_segment_spectrum(bege_ctx* ctx, int32_t seg_id, float* out);
+
+/* Debug: bank rows [k_begin, k_end) as FP32 into HOST `out` ((k_end-k_begin) x L). */
+int bege_get_bank_samples(bege_ctx* ctx, int32_t bank_id, int64_t k_begin, int64_t k_end,
+                          float* out);
+
+/* Segment length N / bank template length L of a handle (0 if unknown). */
+int64_t bege_segment_length(bege_ctx* ctx, int32_t seg_id);
+int64_t bege_bank_length(bege_ctx* ctx, int32_t bank_id);
+
+/* Device bytes currently owned by the context. */
+uint64_t bege_device_bytes(const bege_ctx* ctx);
+
+/* Release a segment, bank or job handle and its device memory (job buffers
+ * return to the context's pool).  Errors: EINVAL for an unknown handle. */
+int bege_release(bege_ctx* ctx, int32_t handle);
+
+/* Message of the last error on the calling thread ("" if none).  ctx may be
+ * NULL. */
+const char* bege_last_error(const bege_ctx* ctx);
+
+/* Library version string. */
+const char* bege_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEGE_H */

@@ -1,0 +1,251 @@
+"""ctypes binding of libbege (include/bege.h): argument marshalling only.
+
+Every function here forwards to the C ABI of the same name; all arithmetic of
+the search runs in the library's CUDA kernels.  Importing this module fails
+loudly when the compiled library is missing: there is no CPU fallback.
+
+Streams are passed as integers (a cudaStream_t, e.g.
+``torch.cuda.current_stream().cuda_stream``); 0 is the legacy default stream.
+Device pointers (``bege_load_segment_device``) are integers too, e.g.
+``tensor.data_ptr()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbege.so")
+
+BEGE_OK = 0
+BEGE_EINVAL = -1
+BEGE_ENOMEM = -2
+BEGE_EBUDGET = -3
+BEGE_EOVERFLOW = -4
+BEGE_ENOTREADY = -5
+BEGE_ETIMEDOUT = -6
+BEGE_ECUDA = -7
+
+STATUS_NAMES = {0: "BEGE_OK", -1: "BEGE_EINVAL", -2: "BEGE_ENOMEM", -3: "BEGE_EBUDGET",
+                -4: "BEGE_EOVERFLOW", -5: "BEGE_ENOTREADY", -6: "BEGE_ETIMEDOUT",
+                -7: "BEGE_ECUDA"}
+
+TAIL_DTYPE = np.dtype([("tmpl", np.uint32), ("lag", np.uint32), ("value", np.float32)])
+
+
+class bege_config(ctypes.Structure):
+    _fields_ = [("fs", ctypes.c_double), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("tail_capacity", ctypes.c_uint64), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class bege_chirp(ctypes.Structure):
+    _fields_ = [("f0", ctypes.c_double), ("fdot", ctypes.c_double)]
+
+
+class bege_tail(ctypes.Structure):
+    _fields_ = [("tmpl", ctypes.c_uint32), ("lag", ctypes.c_uint32), ("value", ctypes.c_float)]
+
+
+assert ctypes.sizeof(bege_tail) == TAIL_DTYPE.itemsize == 12
+
+# name -> (restype, argtypes); every symbol declared in include/bege.h
+_VP = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_PI32 = ctypes.POINTER(ctypes.c_int32)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "bege_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(bege_config)]),
+    "bege_destroy": (ctypes.c_int, [_VP]),
+    "bege_load_segment": (ctypes.c_int, [_VP, _VP, _I64, _I32, _VP, _PI32]),
+    "bege_load_segment_device": (ctypes.c_int, [_VP, _VP, _I64, _I32, _VP, _PI32]),
+    "bege_define_bank": (ctypes.c_int, [_VP, _VP, _I64, ctypes.c_double, ctypes.c_double, _VP,
+                                        _PI32]),
+    "bege_define_bank_samples": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _PI32]),
+    "bege_correlate": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
+    "bege_fetch_tails": (ctypes.c_int, [_VP, _I32, _VP, _I64, _PI64, _PI64]),
+    "bege_query": (ctypes.c_int, [_VP, _I32]),
+    "bege_job_kernel_ms": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_float)]),
+    "bege_get_sigma": (ctypes.c_int, [_VP, _I32, _VP, _I64]),
+    "bege_dump_correlation": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, _VP, _VP]),
+    "bege_get_segment_spectrum": (ctypes.c_int, [_VP, _I32, _VP]),
+    "bege_get_bank_samples": (ctypes.c_int, [_VP, _I32, _I64, _I64, _VP]),
+    "bege_segment_length": (_I64, [_VP, _I32]),
+    "bege_bank_length": (_I64, [_VP, _I32]),
+    "bege_device_bytes": (ctypes.c_uint64, [_VP]),
+    "bege_release": (ctypes.c_int, [_VP, _I32]),
+    "bege_last_error": (ctypes.c_char_p, [_VP]),
+    "bege_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libbege.so (built by ``paper_1708_01609_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libbege.so not built at {path}; run paper_1708_01609_gb300.build")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class BegeError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code: int, where: str, ok=(BEGE_OK,)) -> int:
+    if code not in ok:
+        msg = load_library().bege_last_error(None)
+        raise BegeError(code, where, msg.decode() if msg else "")
+    return code
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class Context:
+    """One libbege context on one CUDA device (method names follow bege.h)."""
+
+    def __init__(self, device: int = 0, fs: float = 4096.0, hbm_budget_bytes: int = 0,
+                 tail_capacity: int = 1 << 20):
+        self.lib = load_library()
+        cfg = bege_config(fs, hbm_budget_bytes, tail_capacity, 0, 0)
+        h = _VP()
+        _check(self.lib.bege_create(ctypes.byref(h), device, ctypes.byref(cfg)), "bege_create")
+        self.h = h
+        self.fs = fs
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(self.lib.bege_destroy(self.h), "bege_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- segments ---------------------------------------------------------
+    def bege_load_segment(self, strain: np.ndarray, channel: int = 0, stream: int = 0) -> int:
+        y = np.ascontiguousarray(strain, dtype=np.float32)
+        sid = _I32()
+        _check(self.lib.bege_load_segment(self.h, _ptr(y), len(y), channel, stream,
+                                          ctypes.byref(sid)), "bege_load_segment")
+        return sid.value
+
+    def bege_load_segment_device(self, ptr: int, n: int, channel: int = 0, stream: int = 0) -> int:
+        sid = _I32()
+        _check(self.lib.bege_load_segment_device(self.h, ptr, n, channel, stream,
+                                                 ctypes.byref(sid)), "bege_load_segment_device")
+        return sid.value
+
+    # -- banks ------------------------------------------------------------
+    def bege_define_bank(self, params: np.ndarray, tau: float = 1.0, taper_frac: float = 0.05,
+                         stream: int = 0) -> int:
+        p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 2)
+        bid = _I32()
+        _check(self.lib.bege_define_bank(self.h, _ptr(p), len(p), tau, taper_frac, stream,
+                                         ctypes.byref(bid)), "bege_define_bank")
+        return bid.value
+
+    def bege_define_bank_samples(self, samples: np.ndarray, stream: int = 0) -> int:
+        w = np.ascontiguousarray(samples, dtype=np.float32)
+        if w.ndim != 2:
+            raise ValueError("samples must be (count, length)")
+        bid = _I32()
+        _check(self.lib.bege_define_bank_samples(self.h, _ptr(w), w.shape[0], w.shape[1], stream,
+                                                 ctypes.byref(bid)), "bege_define_bank_samples")
+        return bid.value
+
+    # -- search -----------------------------------------------------------
+    def bege_correlate(self, seg: int, bank: int, k_begin: int, k_end: int, kappa: float,
+                       stream: int = 0) -> int:
+        jid = _I32()
+        _check(self.lib.bege_correlate(self.h, seg, bank, k_begin, k_end, kappa, stream,
+                                       ctypes.byref(jid)), "bege_correlate")
+        return jid.value
+
+    def bege_fetch_tails(self, job: int, capacity: int | None = None, out: np.ndarray | None = None):
+        """Returns (records as TAIL_DTYPE array, n_total).
+
+        With neither ``capacity`` nor ``out`` the true count is queried first
+        and a buffer of that size is used."""
+        nw, nt = _I64(), _I64()
+        if out is None:
+            if capacity is None:
+                _check(self.lib.bege_fetch_tails(self.h, job, None, 0, ctypes.byref(nw),
+                                                 ctypes.byref(nt)), "bege_fetch_tails",
+                       ok=(BEGE_OK, BEGE_EOVERFLOW))
+                capacity = nt.value
+            out = np.empty(capacity, dtype=TAIL_DTYPE)
+        _check(self.lib.bege_fetch_tails(self.h, job, _ptr(out), len(out), ctypes.byref(nw),
+                                         ctypes.byref(nt)), "bege_fetch_tails",
+               ok=(BEGE_OK, BEGE_EOVERFLOW))
+        return out[: nw.value], nt.value
+
+    def bege_query(self, job: int) -> bool:
+        return _check(self.lib.bege_query(self.h, job), "bege_query",
+                      ok=(BEGE_OK, BEGE_ENOTREADY)) == BEGE_OK
+
+    def bege_job_kernel_ms(self, job: int) -> float:
+        ms = ctypes.c_float()
+        _check(self.lib.bege_job_kernel_ms(self.h, job, ctypes.byref(ms)), "bege_job_kernel_ms")
+        return float(ms.value)
+
+    def bege_get_sigma(self, job: int, count: int) -> np.ndarray:
+        out = np.empty(count, dtype=np.float32)
+        _check(self.lib.bege_get_sigma(self.h, job, _ptr(out), count), "bege_get_sigma")
+        return out
+
+    def bege_dump_correlation(self, seg: int, bank: int, k_begin: int, k_end: int,
+                              stream: int = 0) -> np.ndarray:
+        n = self.lib.bege_segment_length(self.h, seg)
+        out = np.empty((k_end - k_begin, n), dtype=np.float32)
+        _check(self.lib.bege_dump_correlation(self.h, seg, bank, k_begin, k_end, _ptr(out),
+                                              stream), "bege_dump_correlation")
+        return out
+
+    def bege_get_segment_spectrum(self, seg: int) -> np.ndarray:
+        n = self.lib.bege_segment_length(self.h, seg)
+        out = np.empty(n + 2, dtype=np.float32)
+        _check(self.lib.bege_get_segment_spectrum(self.h, seg, _ptr(out)),
+               "bege_get_segment_spectrum")
+        return out[0::2].astype(np.float64) + 1j * out[1::2]
+
+    def bege_get_bank_samples(self, bank: int, k_begin: int, k_end: int) -> np.ndarray:
+        length = self.lib.bege_bank_length(self.h, bank)
+        out = np.empty((k_end - k_begin, length), dtype=np.float32)
+        _check(self.lib.bege_get_bank_samples(self.h, bank, k_begin, k_end, _ptr(out)),
+               "bege_get_bank_samples")
+        return out
+
+    def bege_release(self, handle: int) -> None:
+        _check(self.lib.bege_release(self.h, handle), "bege_release")
+
+    def bege_device_bytes(self) -> int:
+        return int(self.lib.bege_device_bytes(self.h))
+
+
+def bege_version() -> str:
+    return load_library().bege_version().decode()

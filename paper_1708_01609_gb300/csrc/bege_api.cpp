@@ -1,0 +1,705 @@
+// libbege C ABI: contexts, handles, memory accounting and job bookkeeping.
+// The arithmetic of the search lives in bege_kernels.cu; this file validates
+// arguments, owns device memory and enqueues the kernels.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bege_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(BEGE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct PlanHost {
+  bege::Geometry g{};
+  bege::PlanDev dev{};
+  DevBuf tables;
+};
+
+struct Segment {
+  int64_t n = 0;
+  int32_t channel = 0;
+  DevBuf D, AB;
+  std::shared_ptr<PlanHost> plan;
+};
+
+struct Bank {
+  int64_t count = 0, L = 0, Lp = 0;
+  DevBuf w;
+};
+
+struct JobBuffers {
+  DevBuf sigma, recs, counter;
+  int64_t sigma_cap = 0;
+  uint64_t rec_cap = 0;
+};
+
+struct Job {
+  int32_t seg = -1, bank = -1;
+  int64_t k0 = 0, k1 = 0;
+  float kappa = 0.f;
+  std::unique_ptr<JobBuffers> buf;
+  cudaEvent_t done = nullptr;
+  cudaEvent_t k_start = nullptr, k_stop = nullptr;  // around the correlate kernel
+};
+
+static void destroy_job_events(Job* j) {
+  if (j->done) cudaEventDestroy(j->done);
+  if (j->k_start) cudaEventDestroy(j->k_start);
+  if (j->k_stop) cudaEventDestroy(j->k_stop);
+  j->done = j->k_start = j->k_stop = nullptr;
+}
+
+struct bege_ctx {
+  int device = 0;
+  bege_config cfg{};
+  std::mutex mu;
+  uint64_t bytes = 0;
+  int32_t next_id = 1;
+  std::map<int64_t, std::shared_ptr<PlanHost>> plans;  // by N
+  std::map<int32_t, std::unique_ptr<Segment>> segs;
+  std::map<int32_t, std::unique_ptr<Bank>> banks;
+  std::map<int32_t, std::unique_ptr<Job>> jobs;
+  std::vector<std::unique_ptr<JobBuffers>> pool;
+
+  int alloc(DevBuf* b, size_t bytes) {
+    if (cfg.hbm_budget_bytes && this->bytes + bytes > cfg.hbm_budget_bytes)
+      return fail(BEGE_EBUDGET, "device allocation of " + std::to_string(bytes) +
+                                    " bytes exceeds the HBM budget");
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BEGE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b->ptr = p;
+    b->bytes = bytes;
+    this->bytes += bytes;
+    return BEGE_OK;
+  }
+  void release(DevBuf* b) {
+    if (b->ptr) {
+      cudaFree(b->ptr);
+      bytes -= b->bytes;
+    }
+    b->ptr = nullptr;
+    b->bytes = 0;
+  }
+};
+
+namespace {
+
+// exp(-2 pi i k / M) in FP64, rounded once to FP32.
+float2 wexp(int64_t k, int64_t M) {
+  const double a = -2.0 * M_PI * (double)(k % M) / (double)M;
+  return make_float2((float)std::cos(a), (float)std::sin(a));
+}
+
+int get_plan(bege_ctx* ctx, int64_t n, std::shared_ptr<PlanHost>* out) {
+  auto it = ctx->plans.find(n);
+  if (it != ctx->plans.end()) {
+    *out = it->second;
+    return BEGE_OK;
+  }
+  auto p = std::make_shared<PlanHost>();
+  p->g = bege::make_geometry(n);
+  const bege::Geometry& g = p->g;
+  // tables: tw2 [16 R0], tw3 [F], wH [256 S], wR0S [R0 S], w16S [16 S], wS [S], wN [H]
+  const size_t n_tw2 = 16 * g.R0, n_tw3 = g.F, n_wH = 256 * g.S, n_wR0S = g.R0 * g.S,
+               n_w16S = 16 * g.S, n_wS = g.S, n_wN = g.H;
+  std::vector<float2> h(n_tw2 + n_tw3 + n_wH + n_wR0S + n_w16S + n_wS + n_wN);
+  size_t o = 0;
+  const size_t o_tw2 = o;
+  for (int r = 0; r < 16; ++r)
+    for (int k = 0; k < g.R0; ++k) h[o + r * g.R0 + k] = wexp((int64_t)k * r, 16 * g.R0);
+  o += n_tw2;
+  const size_t o_tw3 = o;
+  const int ns3 = g.F / 16;
+  for (int r = 0; r < 16; ++r)
+    for (int k = 0; k < ns3; ++k) h[o + r * ns3 + k] = wexp((int64_t)k * r, g.F);
+  o += n_tw3;
+  const size_t o_wH = o;
+  for (size_t k = 0; k < n_wH; ++k) h[o + k] = wexp((int64_t)k, g.H);
+  o += n_wH;
+  const size_t o_wR0S = o;
+  for (size_t k = 0; k < n_wR0S; ++k) h[o + k] = wexp((int64_t)k, (int64_t)g.R0 * g.S);
+  o += n_wR0S;
+  const size_t o_w16S = o;
+  for (size_t k = 0; k < n_w16S; ++k) h[o + k] = wexp((int64_t)k, 16 * (int64_t)g.S);
+  o += n_w16S;
+  const size_t o_wS = o;
+  for (size_t k = 0; k < n_wS; ++k) h[o + k] = wexp((int64_t)k, g.S);
+  o += n_wS;
+  const size_t o_wN = o;
+  for (size_t k = 0; k < n_wN; ++k) h[o + k] = wexp((int64_t)k, g.N);
+  o += n_wN;
+  int rc = ctx->alloc(&p->tables, h.size() * sizeof(float2));
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpy(p->tables.ptr, h.data(), h.size() * sizeof(float2),
+                             cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    ctx->release(&p->tables);
+    return cuda_fail(e, "plan tables");
+  }
+  const float2* base = static_cast<const float2*>(p->tables.ptr);
+  p->dev.g = g;
+  p->dev.tw2 = base + o_tw2;
+  p->dev.tw3 = base + o_tw3;
+  p->dev.wH = base + o_wH;
+  p->dev.wR0S = base + o_wR0S;
+  p->dev.w16S = base + o_w16S;
+  p->dev.wS = base + o_wS;
+  p->dev.wN = base + o_wN;
+  ctx->plans[n] = p;
+  *out = p;
+  return BEGE_OK;
+}
+
+// Fixed-point representation of x mod 1 in units of 2^-64 cycles.
+unsigned long long frac_to_u64(double x) {
+  x -= std::floor(x);
+  const double s = std::ldexp(x, 32);
+  double hi = std::floor(s);
+  const double rem = s - hi;
+  double lo = std::nearbyint(std::ldexp(rem, 32));
+  if (lo >= 4294967296.0) {
+    lo -= 4294967296.0;
+    hi += 1.0;
+  }
+  const unsigned long long h = (unsigned long long)hi & 0xffffffffull;
+  return (h << 32) + (unsigned long long)lo;
+}
+
+int segment_common(bege_ctx* ctx, const float* y_dev, int64_t n, int32_t channel,
+                   cudaStream_t s, int32_t* seg_id) {
+  std::shared_ptr<PlanHost> plan;
+  int rc = get_plan(ctx, n, &plan);
+  if (rc) return rc;
+  auto seg = std::make_unique<Segment>();
+  seg->n = n;
+  seg->channel = channel;
+  seg->plan = plan;
+  const bege::Geometry& g = plan->g;
+  rc = ctx->alloc(&seg->D, (size_t)(g.H + 1) * sizeof(float2));
+  if (rc) return rc;
+  rc = ctx->alloc(&seg->AB, (size_t)g.H * sizeof(float4));
+  if (rc) {
+    ctx->release(&seg->D);
+    return rc;
+  }
+  cudaError_t e = bege::launch_segment(plan->dev, y_dev, static_cast<float2*>(seg->D.ptr),
+                                       static_cast<float4*>(seg->AB.ptr), s);
+  if (e != cudaSuccess) {
+    ctx->release(&seg->D);
+    ctx->release(&seg->AB);
+    return cuda_fail(e, "segment kernel");
+  }
+  const int32_t id = ctx->next_id++;
+  ctx->segs[id] = std::move(seg);
+  *seg_id = id;
+  return BEGE_OK;
+}
+
+int take_job_buffers(bege_ctx* ctx, int64_t nsig, uint64_t cap, std::unique_ptr<JobBuffers>* out) {
+  for (size_t i = 0; i < ctx->pool.size(); ++i) {
+    if (ctx->pool[i]->sigma_cap >= nsig && ctx->pool[i]->rec_cap >= cap) {
+      *out = std::move(ctx->pool[i]);
+      ctx->pool.erase(ctx->pool.begin() + i);
+      return BEGE_OK;
+    }
+  }
+  auto b = std::make_unique<JobBuffers>();
+  int rc = ctx->alloc(&b->sigma, (size_t)nsig * sizeof(float));
+  if (rc) return rc;
+  rc = ctx->alloc(&b->recs, (size_t)cap * sizeof(bege_tail));
+  if (rc) {
+    ctx->release(&b->sigma);
+    return rc;
+  }
+  rc = ctx->alloc(&b->counter, sizeof(unsigned long long));
+  if (rc) {
+    ctx->release(&b->sigma);
+    ctx->release(&b->recs);
+    return rc;
+  }
+  b->sigma_cap = nsig;
+  b->rec_cap = cap;
+  *out = std::move(b);
+  return BEGE_OK;
+}
+
+Job* find_job(bege_ctx* ctx, int32_t id) {
+  auto it = ctx->jobs.find(id);
+  return it == ctx->jobs.end() ? nullptr : it->second.get();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bege_version(void) { return "bege 0.1 (sm_103a)"; }
+
+const char* bege_last_error(const bege_ctx*) { return g_last_error.c_str(); }
+
+int bege_create(bege_ctx** out, int device, const bege_config* cfg) {
+  if (!out) return fail(BEGE_EINVAL, "out is NULL");
+  *out = nullptr;
+  bege_config c{};
+  c.fs = 4096.0;
+  c.tail_capacity = 1u << 20;
+  if (cfg) {
+    c = *cfg;
+    if (c.fs == 0.0) c.fs = 4096.0;
+    if (c.tail_capacity == 0) c.tail_capacity = 1u << 20;
+  }
+  if (!(c.fs > 0.0) || !std::isfinite(c.fs)) return fail(BEGE_EINVAL, "fs must be positive");
+  if (c.precision != 0) return fail(BEGE_EINVAL, "only precision 0 (FP32) is available");
+  if (c.reserved != 0) return fail(BEGE_EINVAL, "reserved must be 0");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(BEGE_EINVAL, "no such CUDA device");
+  DeviceGuard dg(device);
+  if (!dg.ok) return fail(BEGE_ECUDA, "cudaSetDevice failed");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (prop.major < 10) return fail(BEGE_ECUDA, "libbege needs an sm_103a (Blackwell) GPU");
+  auto* ctx = new bege_ctx();
+  ctx->device = device;
+  ctx->cfg = c;
+  *out = ctx;
+  return BEGE_OK;
+}
+
+int bege_destroy(bege_ctx* ctx) {
+  if (!ctx) return fail(BEGE_EINVAL, "ctx is NULL");
+  {
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto& kv : ctx->jobs) {
+      if (kv.second->done) cudaEventSynchronize(kv.second->done);
+      destroy_job_events(kv.second.get());
+      ctx->release(&kv.second->buf->sigma);
+      ctx->release(&kv.second->buf->recs);
+      ctx->release(&kv.second->buf->counter);
+    }
+    for (auto& b : ctx->pool) {
+      ctx->release(&b->sigma);
+      ctx->release(&b->recs);
+      ctx->release(&b->counter);
+    }
+    for (auto& kv : ctx->segs) {
+      ctx->release(&kv.second->D);
+      ctx->release(&kv.second->AB);
+    }
+    for (auto& kv : ctx->banks) ctx->release(&kv.second->w);
+    for (auto& kv : ctx->plans) ctx->release(&kv.second->tables);
+  }
+  delete ctx;
+  return BEGE_OK;
+}
+
+int bege_load_segment(bege_ctx* ctx, const float* strain, int64_t n, int32_t channel,
+                      void* stream, int32_t* seg_id) {
+  if (!ctx || !strain || !seg_id) return fail(BEGE_EINVAL, "NULL argument");
+  if (!is_pow2(n) || n < 1024 || n > (1 << 17))
+    return fail(BEGE_EINVAL, "n must be a power of two in [2^10, 2^17]");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevBuf tmp;
+  int rc = ctx->alloc(&tmp, (size_t)n * sizeof(float));
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(tmp.ptr, strain, (size_t)n * sizeof(float),
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    ctx->release(&tmp);
+    return cuda_fail(e, "strain upload");
+  }
+  rc = segment_common(ctx, static_cast<const float*>(tmp.ptr), n, channel, s, seg_id);
+  // the segment kernel reads tmp on stream s; wait before freeing it
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  ctx->release(&tmp);
+  if (rc) return rc;
+  if (e2 != cudaSuccess) return cuda_fail(e2, "segment kernel");
+  return BEGE_OK;
+}
+
+int bege_load_segment_device(bege_ctx* ctx, const float* strain_dev, int64_t n, int32_t channel,
+                             void* stream, int32_t* seg_id) {
+  if (!ctx || !strain_dev || !seg_id) return fail(BEGE_EINVAL, "NULL argument");
+  if (!is_pow2(n) || n < 1024 || n > (1 << 17))
+    return fail(BEGE_EINVAL, "n must be a power of two in [2^10, 2^17]");
+  if (reinterpret_cast<uintptr_t>(strain_dev) % 8 != 0)
+    return fail(BEGE_EINVAL, "strain_dev must be 8-byte aligned");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return segment_common(ctx, strain_dev, n, channel, static_cast<cudaStream_t>(stream), seg_id);
+}
+
+int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, double tau,
+                     double taper_frac, void* stream, int32_t* bank_id) {
+  if (!ctx || !params || !bank_id) return fail(BEGE_EINVAL, "NULL argument");
+  if (count <= 0 || count > (int64_t)1 << 31) return fail(BEGE_EINVAL, "count out of range");
+  if (!(tau > 0.0) || !std::isfinite(tau)) return fail(BEGE_EINVAL, "tau must be positive");
+  if (!(taper_frac >= 0.0 && taper_frac <= 1.0)) return fail(BEGE_EINVAL, "taper_frac in [0,1]");
+  const int64_t L = (int64_t)std::llround(tau * ctx->cfg.fs);
+  if (L < 1 || L > (1 << 16)) return fail(BEGE_EINVAL, "tau * fs must be in [1, 2^16]");
+  std::vector<unsigned long long> ab((size_t)count * 2);
+  const double fs = ctx->cfg.fs;
+  for (int64_t k = 0; k < count; ++k) {
+    if (!std::isfinite(params[k].f0) || !std::isfinite(params[k].fdot))
+      return fail(BEGE_EINVAL, "non-finite chirp parameter");
+    ab[2 * k] = frac_to_u64(params[k].f0 / fs);
+    ab[2 * k + 1] = frac_to_u64(0.5 * params[k].fdot / (fs * fs));
+  }
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto bank = std::make_unique<Bank>();
+  bank->count = count;
+  bank->L = L;
+  bank->Lp = (L + 7) / 8 * 8;
+  int rc = ctx->alloc(&bank->w, (size_t)count * bank->Lp * sizeof(float));
+  if (rc) return rc;
+  DevBuf dab;
+  rc = ctx->alloc(&dab, ab.size() * sizeof(unsigned long long));
+  if (rc) {
+    ctx->release(&bank->w);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(dab.ptr, ab.data(), ab.size() * sizeof(unsigned long long),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = bege::launch_bank_chirp(static_cast<unsigned long long*>(dab.ptr), count, L, bank->Lp,
+                                taper_frac, static_cast<float*>(bank->w.ptr), s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  ctx->release(&dab);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    ctx->release(&bank->w);
+    return cuda_fail(e != cudaSuccess ? e : e2, "bank synthesis");
+  }
+  const int32_t id = ctx->next_id++;
+  ctx->banks[id] = std::move(bank);
+  *bank_id = id;
+  return BEGE_OK;
+}
+
+int bege_define_bank_samples(bege_ctx* ctx, const float* samples, int64_t count, int64_t length,
+                             void* stream, int32_t* bank_id) {
+  if (!ctx || !samples || !bank_id) return fail(BEGE_EINVAL, "NULL argument");
+  if (count <= 0 || count > (int64_t)1 << 31) return fail(BEGE_EINVAL, "count out of range");
+  if (length < 1 || length > (1 << 16)) return fail(BEGE_EINVAL, "length must be in [1, 2^16]");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto bank = std::make_unique<Bank>();
+  bank->count = count;
+  bank->L = length;
+  bank->Lp = (length + 7) / 8 * 8;
+  int rc = ctx->alloc(&bank->w, (size_t)count * bank->Lp * sizeof(float));
+  if (rc) return rc;
+  cudaError_t e = cudaMemsetAsync(bank->w.ptr, 0, bank->w.bytes, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(bank->w.ptr, bank->Lp * sizeof(float), samples, length * sizeof(float),
+                          length * sizeof(float), (size_t)count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    ctx->release(&bank->w);
+    return cuda_fail(e, "bank upload");
+  }
+  const int32_t id = ctx->next_id++;
+  ctx->banks[id] = std::move(bank);
+  *bank_id = id;
+  return BEGE_OK;
+}
+
+static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                          int64_t k_end, float kappa, cudaStream_t s, float* dump_dev,
+                          int32_t* job_id) {
+  auto si = ctx->segs.find(seg_id);
+  if (si == ctx->segs.end()) return fail(BEGE_EINVAL, "unknown segment handle");
+  auto bi = ctx->banks.find(bank_id);
+  if (bi == ctx->banks.end()) return fail(BEGE_EINVAL, "unknown bank handle");
+  Segment* seg = si->second.get();
+  Bank* bank = bi->second.get();
+  if (k_begin < 0 || k_end > bank->count || k_begin >= k_end)
+    return fail(BEGE_EINVAL, "template range outside the bank or empty");
+  if (bank->L > seg->n) return fail(BEGE_EINVAL, "template longer than the segment");
+  if (!std::isfinite(kappa) && !(dump_dev && std::isinf(kappa)))
+    return fail(BEGE_EINVAL, "kappa must be finite");
+  if (kappa < 0.f) return fail(BEGE_EINVAL, "kappa must be >= 0");
+  const int64_t nsig = k_end - k_begin;
+  auto job = std::make_unique<Job>();
+  job->seg = seg_id;
+  job->bank = bank_id;
+  job->k0 = k_begin;
+  job->k1 = k_end;
+  job->kappa = kappa;
+  int rc = take_job_buffers(ctx, nsig, ctx->cfg.tail_capacity, &job->buf);
+  if (rc) return rc;
+  cudaError_t e = cudaEventCreateWithFlags(&job->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&job->k_start);
+  if (e == cudaSuccess) e = cudaEventCreate(&job->k_stop);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(job->buf->counter.ptr, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaEventRecord(job->k_start, s);
+  if (e == cudaSuccess) {
+    bege::CorrelateArgs a{};
+    a.AB = static_cast<const float4*>(seg->AB.ptr);
+    a.bank = static_cast<const float*>(bank->w.ptr);
+    a.Lp = bank->Lp;
+    a.k0 = k_begin;
+    a.k1 = k_end;
+    a.kappa = kappa;
+    a.sigma = static_cast<float*>(job->buf->sigma.ptr);
+    a.recs = static_cast<bege_tail*>(job->buf->recs.ptr);
+    a.cap = job->buf->rec_cap;
+    a.counter = static_cast<unsigned long long*>(job->buf->counter.ptr);
+    a.dump = dump_dev;
+    a.max_clusters = 0;
+    e = bege::launch_correlate(seg->plan->dev, a, s);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(job->k_stop, s);
+  if (e == cudaSuccess) e = cudaEventRecord(job->done, s);
+  if (e != cudaSuccess) {
+    destroy_job_events(job.get());
+    ctx->pool.push_back(std::move(job->buf));
+    return cuda_fail(e, "correlate");
+  }
+  const int32_t id = ctx->next_id++;
+  ctx->jobs[id] = std::move(job);
+  *job_id = id;
+  return BEGE_OK;
+}
+
+int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                   int64_t k_end, float kappa, void* stream, int32_t* job_id) {
+  if (!ctx || !job_id) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, kappa,
+                        static_cast<cudaStream_t>(stream), nullptr, job_id);
+}
+
+int bege_job_kernel_ms(bege_ctx* ctx, int32_t job_id, float* ms) {
+  if (!ctx || !ms) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Job* j = find_job(ctx, job_id);
+  if (!j) return fail(BEGE_EINVAL, "unknown job handle");
+  cudaError_t e = cudaEventSynchronize(j->done);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, j->k_start, j->k_stop);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel time");
+  return BEGE_OK;
+}
+
+int bege_query(bege_ctx* ctx, int32_t job_id) {
+  if (!ctx) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Job* j = find_job(ctx, job_id);
+  if (!j) return fail(BEGE_EINVAL, "unknown job handle");
+  cudaError_t e = cudaEventQuery(j->done);
+  if (e == cudaErrorNotReady) return BEGE_ENOTREADY;
+  if (e != cudaSuccess) return cuda_fail(e, "job");
+  return BEGE_OK;
+}
+
+int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capacity,
+                     int64_t* n_written, int64_t* n_total) {
+  if (!ctx || !n_written || !n_total) return fail(BEGE_EINVAL, "NULL argument");
+  if (capacity < 0 || (capacity > 0 && !out)) return fail(BEGE_EINVAL, "bad output buffer");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Job* j = find_job(ctx, job_id);
+  if (!j) return fail(BEGE_EINVAL, "unknown job handle");
+  cudaError_t e = cudaEventSynchronize(j->done);
+  if (e != cudaSuccess) return cuda_fail(e, "job");
+  unsigned long long total = 0;
+  e = cudaMemcpy(&total, j->buf->counter.ptr, sizeof(total), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "tail count");
+  uint64_t ncopy = total;
+  if (ncopy > j->buf->rec_cap) ncopy = j->buf->rec_cap;
+  if (ncopy > (uint64_t)capacity) ncopy = (uint64_t)capacity;
+  if (ncopy) {
+    e = cudaMemcpy(out, j->buf->recs.ptr, ncopy * sizeof(bege_tail), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "tail records");
+  }
+  *n_written = (int64_t)ncopy;
+  *n_total = (int64_t)total;
+  if (ncopy < total)
+    return fail(BEGE_EOVERFLOW, "more tails (" + std::to_string(total) + ") than copied (" +
+                                    std::to_string(ncopy) + ")");
+  return BEGE_OK;
+}
+
+int bege_get_sigma(bege_ctx* ctx, int32_t job_id, float* out, int64_t count) {
+  if (!ctx || !out) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Job* j = find_job(ctx, job_id);
+  if (!j) return fail(BEGE_EINVAL, "unknown job handle");
+  if (count != j->k1 - j->k0) return fail(BEGE_EINVAL, "count must equal k_end - k_begin");
+  cudaError_t e = cudaEventSynchronize(j->done);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(out, j->buf->sigma.ptr, (size_t)count * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "sigma");
+  return BEGE_OK;
+}
+
+int bege_dump_correlation(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                          int64_t k_end, float* out, void* stream) {
+  if (!ctx || !out) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto si = ctx->segs.find(seg_id);
+  if (si == ctx->segs.end()) return fail(BEGE_EINVAL, "unknown segment handle");
+  if (k_end <= k_begin) return fail(BEGE_EINVAL, "empty template range");
+  const int64_t n = si->second->n;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevBuf d;
+  int rc = ctx->alloc(&d, (size_t)(k_end - k_begin) * n * sizeof(float));
+  if (rc) return rc;
+  int32_t job = -1;
+  rc = correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, INFINITY, s,
+                      static_cast<float*>(d.ptr), &job);
+  if (rc) {
+    ctx->release(&d);
+    return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(out, d.ptr, (size_t)(k_end - k_begin) * n * sizeof(float),
+                   cudaMemcpyDeviceToHost);
+  ctx->release(&d);
+  Job* j = find_job(ctx, job);
+  if (j) {
+    destroy_job_events(j);
+    ctx->pool.push_back(std::move(j->buf));
+    ctx->jobs.erase(job);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "dump");
+  return BEGE_OK;
+}
+
+int bege_get_segment_spectrum(bege_ctx* ctx, int32_t seg_id, float* out) {
+  if (!ctx || !out) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto si = ctx->segs.find(seg_id);
+  if (si == ctx->segs.end()) return fail(BEGE_EINVAL, "unknown segment handle");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(out, si->second->D.ptr, si->second->D.bytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "segment spectrum");
+  return BEGE_OK;
+}
+
+int bege_get_bank_samples(bege_ctx* ctx, int32_t bank_id, int64_t k_begin, int64_t k_end,
+                          float* out) {
+  if (!ctx || !out) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto bi = ctx->banks.find(bank_id);
+  if (bi == ctx->banks.end()) return fail(BEGE_EINVAL, "unknown bank handle");
+  Bank* b = bi->second.get();
+  if (k_begin < 0 || k_end > b->count || k_begin >= k_end)
+    return fail(BEGE_EINVAL, "row range outside the bank");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(out, b->L * sizeof(float),
+                     static_cast<const float*>(b->w.ptr) + k_begin * b->Lp, b->Lp * sizeof(float),
+                     b->L * sizeof(float), (size_t)(k_end - k_begin), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "bank samples");
+  return BEGE_OK;
+}
+
+int64_t bege_segment_length(bege_ctx* ctx, int32_t seg_id) {
+  if (!ctx) return 0;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto si = ctx->segs.find(seg_id);
+  return si == ctx->segs.end() ? 0 : si->second->n;
+}
+
+int64_t bege_bank_length(bege_ctx* ctx, int32_t bank_id) {
+  if (!ctx) return 0;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto bi = ctx->banks.find(bank_id);
+  return bi == ctx->banks.end() ? 0 : bi->second->L;
+}
+
+uint64_t bege_device_bytes(const bege_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+int bege_release(bege_ctx* ctx, int32_t handle) {
+  if (!ctx) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto ji = ctx->jobs.find(handle);
+  if (ji != ctx->jobs.end()) {
+    cudaEventSynchronize(ji->second->done);
+    destroy_job_events(ji->second.get());
+    ctx->pool.push_back(std::move(ji->second->buf));
+    ctx->jobs.erase(ji);
+    return BEGE_OK;
+  }
+  auto si = ctx->segs.find(handle);
+  if (si != ctx->segs.end()) {
+    cudaDeviceSynchronize();
+    ctx->release(&si->second->D);
+    ctx->release(&si->second->AB);
+    ctx->segs.erase(si);
+    return BEGE_OK;
+  }
+  auto bi = ctx->banks.find(handle);
+  if (bi != ctx->banks.end()) {
+    cudaDeviceSynchronize();
+    ctx->release(&bi->second->w);
+    ctx->banks.erase(bi);
+    return BEGE_OK;
+  }
+  return fail(BEGE_EINVAL, "unknown handle");
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Register-level DFT kernels and shared-memory Stockham passes for the
+// column FFTs of the correlation (Eq. 3S).  Forward kernel exp(-i ...) as in
+// Eq. A2; the inverse uses exp(+i ...) without the 1/N factor.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace bege {
+
+constexpr int kThreads = 512;  // threads per CTA of every column kernel
+
+// Shared-memory index with one padding slot every 16 complex values: keeps
+// the strided Stockham stores (stride 16 and 17*16) free of bank conflicts.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+template <int F>
+__host__ __device__ constexpr int col_stride() { return F + F / 16; }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// a * b
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cconjmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// multiply by exp(-i t) (forward) or exp(+i t) (inverse), with c = cos t, s = sin t
+template <bool INV>
+__device__ __forceinline__ float2 twc(float2 a, float c, float s) {
+  return INV ? make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.y, c, a.x * s))
+             : make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+}
+
+constexpr float kC1 = 0.92387953251128674f;  // cos(pi/8)
+constexpr float kS1 = 0.38268343236508978f;  // sin(pi/8)
+constexpr float kR2 = 0.70710678118654752f;  // cos(pi/4)
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+// In place, natural order in and out.
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  float2 s02 = cadd(x0, x2), d02 = csub(x0, x2);
+  float2 s13 = cadd(x1, x3), d13 = mul_mi<INV>(csub(x1, x3));
+  x0 = cadd(s02, s13);
+  x2 = csub(s02, s13);
+  x1 = cadd(d02, d13);
+  x3 = csub(d02, d13);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&x)[8]) {
+  float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  float2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  o1 = twc<INV>(o1, kR2, kR2);    // w8^1
+  o2 = mul_mi<INV>(o2);           // w8^2
+  o3 = twc<INV>(o3, -kR2, kR2);   // w8^3
+  x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
+  x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
+  x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
+  x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
+}
+
+// 16 = 4 x 4: DFT4 over the stride-4 index, twiddle w16^(n2 k1), DFT4 over
+// the offset index, then transpose to natural order.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&x)[16]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(x[n2], x[n2 + 4], x[n2 + 8], x[n2 + 12]);
+  // x[n2 + 4 k1] *= w16^(n2 k1)
+  x[5] = twc<INV>(x[5], kC1, kS1);     // m = 1
+  x[6] = twc<INV>(x[6], kR2, kR2);     // m = 2
+  x[7] = twc<INV>(x[7], kS1, kC1);     // m = 3
+  x[9] = twc<INV>(x[9], kR2, kR2);     // m = 2
+  x[10] = mul_mi<INV>(x[10]);          // m = 4
+  x[11] = twc<INV>(x[11], -kR2, kR2);  // m = 6
+  x[13] = twc<INV>(x[13], kS1, kC1);   // m = 3
+  x[14] = twc<INV>(x[14], -kR2, kR2);  // m = 6
+  x[15] = twc<INV>(x[15], -kC1, -kS1); // m = 9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+  float2 t[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = x[4 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x[i] = t[i];
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&x)[R]) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    dft2<INV>(x[0], x[1]);
+  } else if constexpr (R == 4) {
+    dft4<INV>(x[0], x[1], x[2], x[3]);
+  } else if constexpr (R == 8) {
+    dft8<INV>(x);
+  } else {
+    static_assert(R == 16, "radix");
+    dft16<INV>(x);
+  }
+}
+
+// One in-place Stockham pass of radix R over nc columns of length F in
+// shared memory (column c at cols + c * col_stride<F>(), padded indexing).
+// Butterfly j reads col[j + r F/R], twiddles by w(Ns R)^(k r) with
+// k = j mod Ns (table tw[r*Ns + k]), and writes col[(j-k) R + k + r Ns].
+// Butterflies are taken in rounds of kThreads; since F/R divides kThreads
+// every round covers whole columns, so a round can load, synchronise and
+// store without touching the columns of the next round.  Each thread holds
+// one butterfly (R complex values) across a barrier.
+template <int F, int R, bool INV>
+__device__ __forceinline__ void stockham_pass(float2* cols, int nc, int Ns, const float2* tw) {
+  constexpr int NB = F / R;
+  static_assert(kThreads % NB == 0, "rounds must cover whole columns");
+  const int total = nc * NB;
+  const int rounds = (total + kThreads - 1) / kThreads;
+  for (int i = 0; i < rounds; ++i) {
+    const int idx = threadIdx.x + i * kThreads;
+    const bool act = idx < total;
+    const int c = idx / NB, j = idx - c * NB;
+    const int k = j & (Ns - 1);
+    float2 v[R];
+    if (act) {
+      const float2* col = cols + c * col_stride<F>();
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = col[pad(j + r * NB)];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const float2 t = tw[r * Ns + k];
+          v[r] = INV ? cmulc(v[r], t) : cmul(v[r], t);
+        }
+      }
+      dft<R, INV>(v);
+    }
+    __syncthreads();
+    if (act) {
+      float2* col = cols + c * col_stride<F>();
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) col[pad(base + r * Ns)] = v[r];
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace bege

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every symbol of include/bege.h.
+
+CPU-only: no compute call is made.  bege_create is the one call exercised,
+and on a machine without a usable GPU it must fail loudly (BEGE_ECUDA), not
+fall back to the CPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bege.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bege_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1708_01609_gb300 import build
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ["bege_create", "bege_load_segment", "bege_define_bank", "bege_correlate",
+                 "bege_fetch_tails", "bege_get_sigma", "bege_release", "bege_last_error"]:
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1708_01609_gb300 import binding
+    assert set(binding.SIGNATURES) == set(declared_symbols())
+
+
+def test_struct_layouts_match_header():
+    from paper_1708_01609_gb300 import binding
+    assert ctypes.sizeof(binding.bege_tail) == 12
+    assert ctypes.sizeof(binding.bege_chirp) == 16
+    assert ctypes.sizeof(binding.bege_config) == 32
+
+
+def test_version_string(lib):
+    lib.bege_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.bege_version()
+
+
+def test_create_without_gpu_fails_loudly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = lib.bege_create(ctypes.byref(h), 0, None)
+    assert rc == -7  # BEGE_ECUDA
+    lib.bege_last_error.restype = ctypes.c_char_p
+    assert lib.bege_last_error(None)
+
+
+def test_null_arguments_rejected(lib):
+    # argument validation happens before any CUDA call
+    assert lib.bege_create(None, 0, None) == -1
+    assert lib.bege_destroy(None) == -1
+    assert lib.bege_release(None, 1) == -1
