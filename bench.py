@@ -298,7 +298,7 @@ def run_ours(args):
         "roofline": {
             "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "correlate_kernel<4096,4>", "kernel_ms": kernel_ms,
+            "kernel": "correlate_kernel<4096,8,2,256>", "kernel_ms": kernel_ms,
             "flops_per_launch": flops_launch,
             "peak_basis": (f"FP32 ALU: {props.multi_processor_count} SMs x 128 lanes x 2 flops x "
                            f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)"),

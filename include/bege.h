@@ -156,6 +156,27 @@ int64_t bege_bank_length(bege_ctx* ctx, int32_t bank_id);
 /* Device bytes currently owned by the context. */
 uint64_t bege_device_bytes(const bege_ctx* ctx);
 
+/* Launch shapes of the correlate kernel for segment length n.  A shape is
+ * (columns per CTA, threads per CTA); the cluster holds (n / 8192) / columns
+ * CTAs.  bege_list_configs writes up to `max` pairs into `out` as
+ * {nc0, threads0, nc1, threads1, ...} and the number available into *count. */
+int bege_list_configs(bege_ctx* ctx, int64_t n, int32_t* out, int32_t max, int32_t* count);
+
+/* Select the launch shape used by later bege_correlate calls for length n.
+ * EINVAL if the shape is not one of bege_list_configs. */
+int bege_set_config(bege_ctx* ctx, int64_t n, int32_t nc, int32_t threads);
+
+/* The launch shape currently used for length n (the default if none set). */
+int bege_get_config(bege_ctx* ctx, int64_t n, int32_t* nc, int32_t* threads);
+
+/* Autotuner (batching form): time every launch shape for the segment's n on
+ * bank rows [k_begin, k_end) of `bank_id` (`reps` timed runs each after one
+ * warm-up, median of the kernel time), select the fastest for that n and
+ * report its median time in *best_ms.  Synchronous on `stream`; the results
+ * of the timing runs are discarded. */
+int bege_autotune(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin, int64_t k_end,
+                  int32_t reps, void* stream, float* best_ms);
+
 /* Release a segment, bank or job handle and its device memory (job buffers
  * return to the context's pool).  Errors: EINVAL for an unknown handle. */
 int bege_release(bege_ctx* ctx, int32_t handle);

@@ -76,6 +76,11 @@ SIGNATURES = {
     "bege_segment_length": (_I64, [_VP, _I32]),
     "bege_bank_length": (_I64, [_VP, _I32]),
     "bege_device_bytes": (ctypes.c_uint64, [_VP]),
+    "bege_list_configs": (ctypes.c_int, [_VP, _I64, _PI32, _I32, _PI32]),
+    "bege_set_config": (ctypes.c_int, [_VP, _I64, _I32, _I32]),
+    "bege_get_config": (ctypes.c_int, [_VP, _I64, _PI32, _PI32]),
+    "bege_autotune": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, _I32, _VP,
+                                     ctypes.POINTER(ctypes.c_float)]),
     "bege_release": (ctypes.c_int, [_VP, _I32]),
     "bege_last_error": (ctypes.c_char_p, [_VP]),
     "bege_version": (ctypes.c_char_p, []),
@@ -239,6 +244,29 @@ class Context:
         _check(self.lib.bege_get_bank_samples(self.h, bank, k_begin, k_end, _ptr(out)),
                "bege_get_bank_samples")
         return out
+
+    def bege_list_configs(self, n: int) -> list[tuple[int, int]]:
+        buf = (ctypes.c_int32 * 32)()
+        cnt = _I32()
+        _check(self.lib.bege_list_configs(self.h, n, buf, 16, ctypes.byref(cnt)),
+               "bege_list_configs")
+        return [(buf[2 * i], buf[2 * i + 1]) for i in range(min(cnt.value, 16))]
+
+    def bege_set_config(self, n: int, nc: int, threads: int) -> None:
+        _check(self.lib.bege_set_config(self.h, n, nc, threads), "bege_set_config")
+
+    def bege_get_config(self, n: int) -> tuple[int, int]:
+        a, b = _I32(), _I32()
+        _check(self.lib.bege_get_config(self.h, n, ctypes.byref(a), ctypes.byref(b)),
+               "bege_get_config")
+        return a.value, b.value
+
+    def bege_autotune(self, seg: int, bank: int, k_begin: int, k_end: int, reps: int = 3,
+                      stream: int = 0) -> float:
+        ms = ctypes.c_float()
+        _check(self.lib.bege_autotune(self.h, seg, bank, k_begin, k_end, reps, stream,
+                                      ctypes.byref(ms)), "bege_autotune")
+        return float(ms.value)
 
     def bege_release(self, handle: int) -> None:
         _check(self.lib.bege_release(self.h, handle), "bege_release")

@@ -19,7 +19,8 @@ LIB = os.path.join(HERE, "libbege.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
           "-I", os.path.join(HERE, "..", "include")]
-SOURCES = ["bege_kernels.cu", "bege_api.cpp"]
+SOURCES = ["bege_corr_s16.cu", "bege_corr_s8.cu", "bege_corr_s4.cu", "bege_corr_s2.cu",
+           "bege_corr_s1.cu", "bege_segment_bank.cu", "bege_api.cpp"]
 
 
 def nvcc() -> str:
@@ -36,8 +37,6 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
         cmd += ["-lineinfo"]
         if verbose_ptxas:
             cmd += ["-Xptxas", "-v"]
-    else:
-        cmd += ["-x", "cu"] if False else []
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

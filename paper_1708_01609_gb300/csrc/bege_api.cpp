@@ -3,6 +3,7 @@
 // arguments, owns device memory and enqueues the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -101,6 +102,7 @@ struct bege_ctx {
   std::map<int32_t, std::unique_ptr<Bank>> banks;
   std::map<int32_t, std::unique_ptr<Job>> jobs;
   std::vector<std::unique_ptr<JobBuffers>> pool;
+  std::map<int64_t, bege::CorrConfig> configs;  // chosen launch shape per N
 
   int alloc(DevBuf* b, size_t bytes) {
     if (cfg.hbm_budget_bytes && this->bytes + bytes > cfg.hbm_budget_bytes)
@@ -499,7 +501,10 @@ static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
     a.counter = static_cast<unsigned long long*>(job->buf->counter.ptr);
     a.dump = dump_dev;
     a.max_clusters = 0;
-    e = bege::launch_correlate(seg->plan->dev, a, s);
+    auto ci = ctx->configs.find(seg->n);
+    const bege::CorrConfig cc =
+        ci != ctx->configs.end() ? ci->second : bege::default_config(seg->plan->g);
+    e = bege::launch_correlate(seg->plan->dev, a, cc, s);
   }
   if (e == cudaSuccess) e = cudaEventRecord(job->k_stop, s);
   if (e == cudaSuccess) e = cudaEventRecord(job->done, s);
@@ -621,6 +626,84 @@ int bege_dump_correlation(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
     ctx->jobs.erase(job);
   }
   if (e != cudaSuccess) return cuda_fail(e, "dump");
+  return BEGE_OK;
+}
+
+int bege_list_configs(bege_ctx* ctx, int64_t n, int32_t* out, int32_t max, int32_t* count) {
+  if (!ctx || !count || (max > 0 && !out)) return fail(BEGE_EINVAL, "NULL argument");
+  if (!is_pow2(n) || n < 1024 || n > (1 << 17)) return fail(BEGE_EINVAL, "bad segment length");
+  bege::CorrConfig c[8];
+  const int k = bege::correlate_configs(bege::make_geometry(n), c, 8);
+  for (int i = 0; i < k && i < max; ++i) {
+    out[2 * i] = c[i].nc;
+    out[2 * i + 1] = c[i].threads;
+  }
+  *count = k;
+  return BEGE_OK;
+}
+
+int bege_set_config(bege_ctx* ctx, int64_t n, int32_t nc, int32_t threads) {
+  if (!ctx) return fail(BEGE_EINVAL, "NULL argument");
+  if (!is_pow2(n) || n < 1024 || n > (1 << 17)) return fail(BEGE_EINVAL, "bad segment length");
+  const bege::CorrConfig c{nc, threads};
+  if (!bege::config_valid(bege::make_geometry(n), c))
+    return fail(BEGE_EINVAL, "launch shape not compiled for this length");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->configs[n] = c;
+  return BEGE_OK;
+}
+
+int bege_get_config(bege_ctx* ctx, int64_t n, int32_t* nc, int32_t* threads) {
+  if (!ctx || !nc || !threads) return fail(BEGE_EINVAL, "NULL argument");
+  if (!is_pow2(n) || n < 1024 || n > (1 << 17)) return fail(BEGE_EINVAL, "bad segment length");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->configs.find(n);
+  const bege::CorrConfig c =
+      it != ctx->configs.end() ? it->second : bege::default_config(bege::make_geometry(n));
+  *nc = c.nc;
+  *threads = c.threads;
+  return BEGE_OK;
+}
+
+int bege_autotune(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin, int64_t k_end,
+                  int32_t reps, void* stream, float* best_ms) {
+  if (!ctx || !best_ms || reps < 1) return fail(BEGE_EINVAL, "bad argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto si = ctx->segs.find(seg_id);
+  if (si == ctx->segs.end()) return fail(BEGE_EINVAL, "unknown segment handle");
+  const int64_t n = si->second->n;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bege::CorrConfig cand[8];
+  const int nc = bege::correlate_configs(si->second->plan->g, cand, 8);
+  float best = 0.f;
+  bege::CorrConfig pick = bege::default_config(si->second->plan->g);
+  for (int i = 0; i < nc; ++i) {
+    ctx->configs[n] = cand[i];
+    std::vector<float> t;
+    for (int r = 0; r <= reps; ++r) {
+      int32_t job = -1;
+      int rc = correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, 1e30f, s, nullptr, &job);
+      if (rc) return rc;
+      Job* j = find_job(ctx, job);
+      float ms = 0.f;
+      cudaError_t e = cudaEventSynchronize(j->done);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, j->k_start, j->k_stop);
+      destroy_job_events(j);
+      ctx->pool.push_back(std::move(j->buf));
+      ctx->jobs.erase(job);
+      if (e != cudaSuccess) return cuda_fail(e, "autotune");
+      if (r > 0) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    const float med = t[t.size() / 2];
+    if (i == 0 || med < best) {
+      best = med;
+      pick = cand[i];
+    }
+  }
+  ctx->configs[n] = pick;
+  *best_ms = best;
   return BEGE_OK;
 }
 

@@ -1,4 +1,4 @@
-// CUDA kernels of libbege (sm_103a).
+// Kernels of the matched-filter hot path, templated on the geometry.
 //
 // Matched filtering by FFT (van Putten, arXiv:1708.01609, Eq. 3S): for a
 // real segment y (N samples) and a real template w (L <= N samples,
@@ -26,14 +26,18 @@
 // Residue columns (four-step with a pruned first step).  Bin j = S a + b,
 // a < F, b < S, H = S F.  Forward:
 //     Z_{Sa+b} = FFT_F(u_b)[a],  u_b[m1] = wH^(b m1) sum_{m2<S} z[m1+F m2] wS^(b m2);
-// a template of L <= 2F samples has z = 0 beyond F, so only m2 = 0 remains.
-// Inverse: with n = n1 + F n2,
+// a template of L <= 2F samples has z = 0 beyond F, so only m2 = 0 remains
+// (and with L <= F the upper half of u_b is zero as well).  Inverse, with
+// n = n1 + F n2,
 //     yo[n1 + F n2] = (1/H) sum_b wS^(-b n2) T_b[n1],
 //     T_b[n1] = wH^(-b n1) IFFT_F(Y_{S.+b})[n1].
 // Column b pairs with column S-b (bins j and H-j); columns {0, S/2} and
-// {i, S-i} form units.  A CTA owns whole units; the C CTAs of a cluster hold
-// all S columns and read each other's columns through distributed shared
-// memory only in the final S-point combine.
+// {i, S-i} form units.  A CTA owns whole units (NC columns); the C = S/NC
+// CTAs of a thread-block cluster hold all S columns and read each other's
+// columns through distributed shared memory only in the final S-point
+// combine.
+#pragma once
+
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -42,23 +46,9 @@
 #include "bege_fft.cuh"
 #include "bege_internal.h"
 
-namespace cg = cooperative_groups;
-
 namespace bege {
 
-Geometry make_geometry(int64_t n) {
-  Geometry g{};
-  g.N = (int)n;
-  g.H = g.N / 2;
-  g.F = g.H < 4096 ? g.H : 4096;
-  g.S = g.H / g.F;
-  g.R0 = g.F / 256;
-  g.C = g.S >= 8 ? g.S / 4 : 1;
-  g.NC = g.S == 1 ? 1 : g.S / g.C;
-  const int units = g.S == 1 ? 1 : g.S / 2;
-  g.UPC = units / g.C;
-  return g;
-}
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // Shared-memory layout: compile-time offsets for (F, NC) so every access is
@@ -79,8 +69,7 @@ struct Lay {
   static constexpr size_t colptr = ws + align16(16 * 8);
   static constexpr size_t red = colptr + align16(16 * 8);
   static constexpr size_t sigpart = red + align16(32 * 4);
-  static constexpr size_t slotb = sigpart + align16(4);
-  static constexpr size_t total = slotb + align16(4 * 4);
+  static constexpr size_t total = sigpart + align16(4);
 };
 
 extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -99,78 +88,70 @@ struct Smem {
   static __device__ __forceinline__ float2** colptr() { return reinterpret_cast<float2**>(smem_raw + L::colptr); }
   static __device__ __forceinline__ float* red() { return reinterpret_cast<float*>(smem_raw + L::red); }
   static __device__ __forceinline__ float* sigpart() { return reinterpret_cast<float*>(smem_raw + L::sigpart); }
-  static __device__ __forceinline__ int* slotb() { return reinterpret_cast<int*>(smem_raw + L::slotb); }
 };
 
-template <int F, int NC>
-constexpr size_t smem_bytes() { return Lay<F, NC>::total; }
-
-size_t correlate_smem_bytes(const Geometry& g) {
-  if (g.F == 4096) {
-    if (g.NC == 4) return smem_bytes<4096, 4>();
-    if (g.NC == 2) return smem_bytes<4096, 2>();
-    return smem_bytes<4096, 1>();
+// Column ownership for S columns split over C = S/NC CTAs.
+template <int S, int NC>
+struct ColMap {
+  static_assert(S == 1 ? NC == 1 : (NC % 2 == 0 && S % NC == 0), "column split");
+  static constexpr int C = S == 1 ? 1 : S / NC;
+  static constexpr int UPC = S == 1 ? 1 : NC / 2;
+  // column b held by local slot c of the CTA with cluster rank `rank`
+  static __device__ __forceinline__ int slot_column(int rank, int c) {
+    if constexpr (S == 1) {
+      return 0;
+    } else {
+      const int ug = rank * UPC + (c >> 1);
+      const int second = c & 1;
+      if (ug == 0) return second ? S / 2 : 0;
+      return second ? S - ug : ug;
+    }
   }
-  if (g.F == 2048) return smem_bytes<2048, 1>();
-  if (g.F == 1024) return smem_bytes<1024, 1>();
-  return smem_bytes<512, 1>();
-}
-
-// Column b held by slot c of the CTA with cluster rank `rank`.
-__device__ __forceinline__ int slot_column(const Geometry& g, int rank, int c) {
-  if (g.S == 1) return 0;
-  const int ug = rank * g.UPC + (c >> 1);
-  const int second = c & 1;
-  if (ug == 0) return second ? g.S / 2 : 0;
-  return second ? g.S - ug : ug;
-}
-
-// Owner CTA rank and slot of column b.
-__device__ __forceinline__ void column_home(const Geometry& g, int b, int* owner, int* slot) {
-  if (g.S == 1) {
-    *owner = 0;
-    *slot = 0;
-    return;
+  // owner rank and local slot of column b
+  static __device__ __forceinline__ void home(int b, int* owner, int* slot) {
+    if constexpr (S == 1) {
+      *owner = 0;
+      *slot = 0;
+    } else {
+      int unit, second;
+      if (b == 0) {
+        unit = 0; second = 0;
+      } else if (b == S / 2) {
+        unit = 0; second = 1;
+      } else if (b < S / 2) {
+        unit = b; second = 0;
+      } else {
+        unit = S - b; second = 1;
+      }
+      *owner = unit / UPC;
+      *slot = 2 * (unit % UPC) + second;
+    }
   }
-  int unit, second;
-  if (b == 0) {
-    unit = 0; second = 0;
-  } else if (b == g.S / 2) {
-    unit = 0; second = 1;
-  } else if (b < g.S / 2) {
-    unit = b; second = 0;
-  } else {
-    unit = g.S - b; second = 1;
-  }
-  *owner = unit / g.UPC;
-  *slot = 2 * (unit % g.UPC) + second;
-}
+};
 
 // Load the per-N twiddle tables into shared memory and resolve the
 // (possibly remote) address of every column.
-template <int F, int NC>
+template <int F, int S, int NC, int T>
 __device__ void setup_tables(const PlanDev& p, int rank, bool map_columns) {
   using SM = Smem<F, NC>;
-  const Geometry& g = p.g;
+  using CM = ColMap<S, NC>;
   const int t = threadIdx.x;
-  for (int i = t; i < F; i += kThreads) SM::tw3()[i] = p.tw3[i];
-  for (int i = t; i < 16 * (F / 256); i += kThreads) SM::tw2()[i] = p.tw2[i];
-  for (int i = t; i < NC * 256; i += kThreads) {
+  for (int i = t; i < F; i += T) SM::tw3()[i] = p.tw3[i];
+  for (int i = t; i < 16 * (F / 256); i += T) SM::tw2()[i] = p.tw2[i];
+  for (int i = t; i < NC * 256; i += T) {
     const int c = i >> 8, j = i & 255;
-    const int b = slot_column(g, rank, c);
-    SM::twin()[i] = p.wH[b * j];
+    SM::twin()[i] = p.wH[CM::slot_column(rank, c) * j];
   }
-  for (int i = t; i < NC * 16; i += kThreads) {
+  for (int i = t; i < NC * 16; i += T) {
     const int c = i >> 4, r = i & 15;
-    const int b = slot_column(g, rank, c);
+    const int b = CM::slot_column(rank, c);
     SM::rin()[i] = r < F / 256 ? p.wR0S[b * r] : make_float2(1.f, 0.f);
     SM::rout()[i] = cconj(p.w16S[b * r]);
   }
-  if (t < 16) SM::ws()[t] = t < g.S ? p.wS[t] : make_float2(1.f, 0.f);
-  if (t < NC) SM::slotb()[t] = slot_column(g, rank, t);
-  if (map_columns && t < g.S) {
+  if (t < 16) SM::ws()[t] = t < S ? p.wS[t] : make_float2(1.f, 0.f);
+  if (map_columns && t < S) {
     int owner, slot;
-    column_home(g, t, &owner, &slot);
+    CM::home(t, &owner, &slot);
     cg::cluster_group cl = cg::this_cluster();
     float2* base = cl.map_shared_rank(SM::cols(), (unsigned)owner);
     SM::colptr()[t] = base + slot * col_stride<F>();
@@ -179,43 +160,49 @@ __device__ void setup_tables(const PlanDev& p, int rank, bool map_columns) {
 
 // First forward pass (radix R0 = F/256, Ns = 1) fused with the load of
 // u_b[m1] = wH^(b m1) sum_{m2} z[m1 + F m2] wS^(b m2) from global memory.
-// src holds nz complex samples z[m] (interleaved floats).
-template <int F, int NC>
-__device__ __forceinline__ void fwd_first_pass(int S, const float* __restrict__ src, int nz,
+// src holds nz complex samples z[m] (interleaved floats).  HALFZ: nz <= F/2
+// and the upper half of every radix-16 input vector is zero.
+template <int F, int S, int NC, int T, bool HALFZ>
+__device__ __forceinline__ void fwd_first_pass(int rank, const float* __restrict__ src, int nz,
                                                int nfold) {
   using SM = Smem<F, NC>;
+  using CM = ColMap<S, NC>;
   constexpr int R0 = F / 256;
+  constexpr int RL = HALFZ ? R0 / 2 : R0;  // inputs that can be non-zero
   constexpr int total = NC * 256;
   const float2* z = reinterpret_cast<const float2*>(src);
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int idx = threadIdx.x + i * kThreads;
-    if (idx < total) {
+  for (int i = 0; i < (total + T - 1) / T; ++i) {
+    const int idx = threadIdx.x + i * T;
+    if ((total % T == 0) || idx < total) {
       const int c = idx >> 8, j = idx & 255;
       float2 v[R0];
 #pragma unroll
       for (int r = 0; r < R0; ++r) {
         const int m1 = j + r * 256;
         float2 acc = make_float2(0.f, 0.f);
-        if (m1 < nz) acc = __ldg(z + m1);
-        if (nfold > 1) {
-          const int b = SM::slotb()[c];
-          for (int m2 = 1; m2 < nfold; ++m2) {
-            const int m = m1 + F * m2;
-            if (m < nz) acc = cadd(acc, cmul(__ldg(z + m), SM::ws()[(b * m2) & (S - 1)]));
+        if (r < RL) {
+          if (m1 < nz) acc = __ldg(z + m1);
+          if (!HALFZ && nfold > 1) {
+            const int b = CM::slot_column(rank, c);
+            for (int m2 = 1; m2 < nfold; ++m2) {
+              const int m = m1 + F * m2;
+              if (m < nz) acc = cadd(acc, cmul(__ldg(z + m), SM::ws()[(b * m2) & (S - 1)]));
+            }
           }
         }
         v[r] = acc;
       }
-      if (S > 1) {
+      if constexpr (S > 1) {
         const float2 tj = SM::twin()[c * 256 + j];
+        const float2* rin = SM::rin() + c * 16;
 #pragma unroll
-        for (int r = 0; r < R0; ++r) v[r] = cmul(cmul(v[r], tj), SM::rin()[c * 16 + r]);
+        for (int r = 0; r < RL; ++r) v[r] = cmul(cmul(v[r], tj), rin[r]);
       }
-      dft<R0, false>(v);
-      float2* col = SM::col(c);
+      dft<R0, false, HALFZ>(v);
+      float2* col = SM::col(c) + pad(j * R0);
 #pragma unroll
-      for (int r = 0; r < R0; ++r) col[pad(j * R0 + r)] = v[r];
+      for (int r = 0; r < R0; ++r) col[r] = v[r];  // R0 <= 16 consecutive: one pad group
     }
   }
   __syncthreads();
@@ -224,75 +211,78 @@ __device__ __forceinline__ void fwd_first_pass(int S, const float* __restrict__ 
 // Last inverse pass (radix 16, Ns = F/16) fused with the output twiddle
 // T_b[n1] = wH^(-b n1) x[n1], n1 = k + r F/16, factored as
 // conj(wH^(b k)) * w(16 S)^(-b r).
-template <int F, int NC>
-__device__ __forceinline__ void inv_last_pass(int S) {
+template <int F, int S, int NC, int T>
+__device__ __forceinline__ void inv_last_pass() {
   using SM = Smem<F, NC>;
   constexpr int NB = F / 16;
   constexpr int Ns = F / 16;
   constexpr int total = NC * NB;
-  constexpr int rounds = (total + kThreads - 1) / kThreads;
+  constexpr int rounds = (total + T - 1) / T;
+  constexpr int step = Ns + Ns / 16;
 #pragma unroll
   for (int i = 0; i < rounds; ++i) {
-    const int idx = threadIdx.x + i * kThreads;
-    const bool act = idx < total;
+    const int idx = threadIdx.x + i * T;
+    const bool act = (total % T == 0) || idx < total;
     const int c = idx / NB, j = idx - c * NB;
     float2 v[16];
     if (act) {
-      const float2* col = SM::col(c);
+      const float2* col = SM::col(c) + pad(j);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) v[r] = col[pad(j + r * NB)];
+      for (int r = 0; r < 16; ++r) v[r] = col[r * step];
+      const float2* t3 = SM::tw3() + j;
 #pragma unroll
-      for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], SM::tw3()[r * Ns + j]);
+      for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], t3[r * Ns]);
       dft<16, true>(v);
-      if (S > 1) {
+      if constexpr (S > 1) {
         const float2 tk = SM::twin()[c * 256 + j];
+        const float2* ro = SM::rout() + c * 16;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = cmul(cmulc(v[r], tk), SM::rout()[c * 16 + r]);
+        for (int r = 0; r < 16; ++r) v[r] = cmul(cmulc(v[r], tk), ro[r]);
       }
     }
     __syncthreads();
     if (act) {
-      float2* col = SM::col(c);
+      float2* col = SM::col(c) + pad(j);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) col[pad(j + r * Ns)] = v[r];
+      for (int r = 0; r < 16; ++r) col[r * step] = v[r];
     }
   }
   __syncthreads();
 }
 
-template <int F, int NC>
-__device__ __forceinline__ void forward_columns(int S, const float* src, int nz, int nfold) {
+template <int F, int S, int NC, int T, bool HALFZ>
+__device__ __forceinline__ void forward_columns(int rank, const float* src, int nz, int nfold) {
   using SM = Smem<F, NC>;
   constexpr int R0 = F / 256;
-  fwd_first_pass<F, NC>(S, src, nz, nfold);
-  stockham_pass<F, 16, false>(SM::cols(), NC, R0, SM::tw2());
-  stockham_pass<F, 16, false>(SM::cols(), NC, 16 * R0, SM::tw3());
+  fwd_first_pass<F, S, NC, T, HALFZ>(rank, src, nz, nfold);
+  stockham_pass<F, NC, T, 16, R0, false>(SM::cols(), SM::tw2());
+  stockham_pass<F, NC, T, 16, 16 * R0, false>(SM::cols(), SM::tw3());
 }
 
-template <int F, int NC>
-__device__ __forceinline__ void inverse_columns(int S) {
+template <int F, int S, int NC, int T>
+__device__ __forceinline__ void inverse_columns() {
   using SM = Smem<F, NC>;
   constexpr int R0 = F / 256;
-  stockham_pass<F, R0, true>(SM::cols(), NC, 1, nullptr);
-  stockham_pass<F, 16, true>(SM::cols(), NC, R0, SM::tw2());
-  inv_last_pass<F, NC>(S);
+  stockham_pass<F, NC, T, R0, 1, true>(SM::cols(), nullptr);
+  stockham_pass<F, NC, T, 16, R0, true>(SM::cols(), SM::tw2());
+  inv_last_pass<F, S, NC, T>();
 }
 
-// Enumerate the bin pairs (j, H-j) held by this CTA.  Unit 0 holds column 0
-// (pairs a <-> (F-a) mod F, with a = 0 and a = F/2 paired with themselves)
-// and column S/2 (pairs a <-> F-1-a); unit i holds columns i and S-i (pairs
+// The bin pairs (j, H-j) held by a unit.  Unit 0 holds column 0 (pairs
+// a <-> (F-a) mod F, with a = 0 and a = F/2 paired with themselves) and
+// column S/2 (pairs a <-> F-1-a); unit i holds columns i and S-i (pairs
 // (i, a) <-> (S-i, F-1-a)).
 struct PairItem {
   int b, a, bp, ap, sj, sp;  // columns, rows, local slots
 };
 
-template <int F>
-__device__ __forceinline__ int unit_items(int S, int ug) {
+template <int F, int S>
+__device__ __forceinline__ int unit_items(int ug) {
   return ug == 0 ? (S >= 2 ? F + 1 : F / 2 + 1) : F;
 }
 
-template <int F>
-__device__ __forceinline__ PairItem pair_item(int S, int ug, int ui, int it) {
+template <int F, int S>
+__device__ __forceinline__ PairItem pair_item(int ug, int ui, int it) {
   PairItem p;
   if (ug == 0) {
     if (it <= F / 2) {
@@ -316,26 +306,148 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // ---------------------------------------------------------------------------
-// S1: segment spectrum D and product coefficients A, B
+// Fused middle of the pipeline for F = 4096 (radix 16 x 16 x 16): the last
+// forward pass, the spectral product with the Parseval sum, and the first
+// inverse pass, in registers.
+//
+// Forward pass 3 (Ns = 256) reads and writes the rows j + 256 r of its
+// butterfly j, and inverse pass 1 (Ns = 1) reads the same rows, so one thread
+// can carry a butterfly from the forward FFT into the inverse FFT.  The bin
+// (b, j + 256 r) pairs with (S-b, (255-j) + 256 (15-r)) (column 0: with
+// (0, (256-j) + 256 (15-r)), column S/2: with (S/2, (255-j) + 256 (15-r))),
+// i.e. with row 15-r of the mirror butterfly, so a thread that holds a
+// butterfly and its mirror forms every Y of both.  Items (256 per unit):
+//   generic unit ug:  (slot 2ui, j) with (slot 2ui+1, 255-j),   j < 256
+//   unit 0, it < 128: column 0, (j, 256-j); it = 0 holds the two
+//                     self-mirrored butterflies 0 and 128
+//   unit 0, it >= 128: column S/2, (j, 255-j), j = it - 128
+// Returns this thread's sum of |Y|^2; ends with the stores of inverse pass 1
+// (callers synchronise before reading the columns).
 // ---------------------------------------------------------------------------
-template <int F, int NC>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int S, int NC, int T>
+__device__ __forceinline__ float fused_mid(int rank, const float4* __restrict__ AB,
+                                           float* red_warp) {
+  constexpr int F = 4096;
+  using SM = Smem<F, NC>;
+  using CM = ColMap<S, NC>;
+  constexpr int UPC = CM::UPC;
+  constexpr int items = S == 1 ? 128 : 256;  // per unit
+  static_assert(T >= items * UPC, "one item per thread");
+  constexpr int step = 256 + 16;             // padded distance of rows r -> r + 1
+  const int t = threadIdx.x;
+  const bool act = t < items * UPC;
+  const int ui = t / items, it = t - ui * items;
+  const int ug = rank * UPC + ui;
+  // columns and butterflies of the item
+  int sa, sb, ja, jb, ba, bb;
+  bool self0 = false;  // column 0, butterflies 0 and 128 (each its own mirror)
+  if (ug == 0 && it < 128) {
+    sa = sb = 2 * ui; ba = bb = 0;
+    ja = it; jb = it == 0 ? 128 : 256 - it;
+    self0 = (it == 0);
+  } else if (ug == 0) {
+    sa = sb = 2 * ui + 1; ba = bb = S / 2;
+    ja = it - 128; jb = 255 - ja;
+  } else {
+    sa = 2 * ui; sb = 2 * ui + 1; ba = ug; bb = S - ug;
+    ja = it; jb = 255 - it;
+  }
+  float2 za[16], zb[16];
+  float acc = 0.f;
+  if (act) {
+    const float2* pa = SM::col(sa) + pad(ja);
+    const float2* pb = SM::col(sb) + pad(jb);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      za[r] = pa[r * step];
+      zb[r] = pb[r * step];
+    }
+    const float2* ta = SM::tw3() + ja;
+    const float2* tb = SM::tw3() + jb;
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+      za[r] = cmul(za[r], ta[r * 256]);
+      zb[r] = cmul(zb[r], tb[r * 256]);
+    }
+    dft<16, false>(za);
+    dft<16, false>(zb);
+    const float4* aba = AB + ba * F + ja;
+    const float4* abb = AB + bb * F + jb;
+    if (!self0) {
+      // za[r] (row ja + 256 r) pairs with zb[15 - r] (row jb + 256 (15 - r))
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const float4 p = __ldcg(aba + 256 * r);
+        const float4 q = __ldcg(abb + 256 * (15 - r));
+        const float2 x = za[r], y = zb[15 - r];
+        const float2 ya = cadd(cconjmul(x, make_float2(p.x, p.y)), cmul(y, make_float2(p.z, p.w)));
+        const float2 yb = cadd(cconjmul(y, make_float2(q.x, q.y)), cmul(x, make_float2(q.z, q.w)));
+        acc = fmaf(ya.x, ya.x, fmaf(ya.y, ya.y, acc));
+        acc = fmaf(yb.x, yb.x, fmaf(yb.y, yb.y, acc));
+        za[r] = ya;
+        zb[15 - r] = yb;
+      }
+    } else {
+      // butterfly 0: rows 256 r pair with 256 ((16 - r) mod 16); r = 0, 8 self
+      float2 ya[16], yb[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int rp = (16 - r) & 15;
+        const float4 p = __ldcg(aba + 256 * r);
+        ya[r] = cadd(cconjmul(za[r], make_float2(p.x, p.y)), cmul(za[rp], make_float2(p.z, p.w)));
+        acc = fmaf(ya[r].x, ya[r].x, fmaf(ya[r].y, ya[r].y, acc));
+      }
+      // butterfly 128: rows 128 + 256 r pair with 128 + 256 (15 - r)
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const float4 q = __ldcg(abb + 256 * r);
+        yb[r] = cadd(cconjmul(zb[r], make_float2(q.x, q.y)), cmul(zb[15 - r], make_float2(q.z, q.w)));
+        acc = fmaf(yb[r].x, yb[r].x, fmaf(yb[r].y, yb[r].y, acc));
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        za[r] = ya[r];
+        zb[r] = yb[r];
+      }
+    }
+    dft<16, true>(za);
+    dft<16, true>(zb);
+  }
+  acc = warp_sum(acc);
+  if ((t & 31) == 0) red_warp[t >> 5] = acc;
+  __syncthreads();  // every load of the columns is done
+  if (act) {
+    // inverse pass 1 (Ns = 1): butterfly j writes rows 16 j + r
+    float2* qa = SM::col(sa) + pad(16 * ja);
+    float2* qb = SM::col(sb) + pad(16 * jb);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) qa[r] = za[r];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) qb[r] = zb[r];
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// S1: segment spectrum D and product coefficients A, B (grid: C CTAs)
+// ---------------------------------------------------------------------------
+template <int F, int S, int NC, int T>
+__global__ void __launch_bounds__(T, 1)
 segment_kernel(PlanDev p, const float* __restrict__ y, float2* __restrict__ D,
                float4* __restrict__ AB) {
   using SM = Smem<F, NC>;
-  const Geometry g = p.g;
-  const int S = g.S;
+  constexpr int UPC = ColMap<S, NC>::UPC;
+  const int H = p.g.H;
   const int rank = blockIdx.x;
-  constexpr int UPC = NC == 1 ? 1 : NC / 2;
-  setup_tables<F, NC>(p, rank, false);
+  setup_tables<F, S, NC, T>(p, rank, false);
   __syncthreads();
-  forward_columns<F, NC>(S, y, g.H, S);
+  forward_columns<F, S, NC, T, false>(rank, y, H, S);
 
   for (int ui = 0; ui < UPC; ++ui) {
     const int ug = rank * UPC + ui;
-    const int count = unit_items<F>(S, ug);
-    for (int it = threadIdx.x; it < count; it += kThreads) {
-      const PairItem q = pair_item<F>(S, ug, ui, it);
+    const int count = unit_items<F, S>(ug);
+    for (int it = threadIdx.x; it < count; it += T) {
+      const PairItem q = pair_item<F, S>(ug, ui, it);
       const float2 zj = SM::col(q.sj)[pad(q.a)];
       const float2 zp = SM::col(q.sp)[pad(q.ap)];
       const int j = S * q.a + q.b;
@@ -371,7 +483,7 @@ segment_kernel(PlanDev p, const float* __restrict__ y, float2* __restrict__ D,
         AB[q.bp * F + q.ap] = coeffs(p.wN[jp], Djp, cHjp);
         D[jp] = Djp;
       }
-      if (j == 0) D[g.H] = DH;
+      if (j == 0) D[H] = DH;
     }
   }
 }
@@ -379,25 +491,27 @@ segment_kernel(PlanDev p, const float* __restrict__ y, float2* __restrict__ D,
 // ---------------------------------------------------------------------------
 // S2-S6: template spectrum, product, sigma, inverse FFT, threshold, compaction
 // ---------------------------------------------------------------------------
-template <int F, int NC, int SS>
-__device__ __forceinline__ void combine_and_emit(int C, int H, int rank, float thr,
-                                                 uint32_t tmpl, int64_t krow,
-                                                 const CorrelateArgs& a) {
+template <int F, int S, int NC, int T>
+__device__ __forceinline__ void combine_and_emit(int H, int rank, float thr, uint32_t tmpl,
+                                                 int64_t krow, const CorrelateArgs& a) {
   using SM = Smem<F, NC>;
-  const int per = F / C;
-  const int iters = per / kThreads;
+  constexpr int C = ColMap<S, NC>::C;
+  constexpr int per = F / C;
+  static_assert(per % T == 0, "combine rounds");
   const int lane = threadIdx.x & 31;
   const float invH = 1.0f / (float)H;
   float2* const* colptr = SM::colptr();
-  for (int it = 0; it < iters; ++it) {
-    const int n1 = rank * per + it * kThreads + threadIdx.x;
-    float2 t[SS];
+#pragma unroll 1
+  for (int it = 0; it < per / T; ++it) {
+    const int n1 = rank * per + it * T + threadIdx.x;
+    const int pn1 = pad(n1);
+    float2 t[S];
 #pragma unroll
-    for (int b = 0; b < SS; ++b) t[b] = colptr[b][pad(n1)];
-    dft<SS, true>(t);
+    for (int b = 0; b < S; ++b) t[b] = colptr[b][pn1];
+    dft<S, true>(t);
     uint32_t mask = 0;
 #pragma unroll
-    for (int n2 = 0; n2 < SS; ++n2) {
+    for (int n2 = 0; n2 < S; ++n2) {
       t[n2] = cscale(t[n2], invH);
       mask |= (fabsf(t[n2].x) > thr ? 1u : 0u) << (2 * n2);
       mask |= (fabsf(t[n2].y) > thr ? 1u : 0u) << (2 * n2 + 1);
@@ -405,7 +519,7 @@ __device__ __forceinline__ void combine_and_emit(int C, int H, int rank, float t
     if (a.dump) {
       float2* row = reinterpret_cast<float2*>(a.dump) + krow * (int64_t)H;
 #pragma unroll
-      for (int n2 = 0; n2 < SS; ++n2) row[n1 + F * n2] = t[n2];
+      for (int n2 = 0; n2 < S; ++n2) row[n1 + F * n2] = t[n2];
     }
     if (__any_sync(0xffffffffu, mask != 0u)) {
       const int cnt = __popc(mask);
@@ -421,7 +535,7 @@ __device__ __forceinline__ void combine_and_emit(int C, int H, int rank, float t
       base = __shfl_sync(0xffffffffu, base, 31);
       unsigned long long pos = base + (unsigned long long)(incl - cnt);
 #pragma unroll
-      for (int n2 = 0; n2 < SS; ++n2) {
+      for (int n2 = 0; n2 < S; ++n2) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           if ((mask >> (2 * n2 + e)) & 1u) {
@@ -439,16 +553,16 @@ __device__ __forceinline__ void combine_and_emit(int C, int H, int rank, float t
   }
 }
 
-template <int F, int NC>
-__global__ void __launch_bounds__(kThreads, 1) correlate_kernel(PlanDev p, CorrelateArgs a) {
+template <int F, int S, int NC, int T, int MINB, bool HALFZ>
+__global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, CorrelateArgs a) {
   using SM = Smem<F, NC>;
-  constexpr int UPC = NC == 1 ? 1 : NC / 2;
+  using CM = ColMap<S, NC>;
+  constexpr int C = CM::C;
+  constexpr int UPC = CM::UPC;
   cg::cluster_group cluster = cg::this_cluster();
-  const int S = p.g.S;
-  const int C = S >= 2 * NC ? S / NC : 1;
   const int N = p.g.N, H = p.g.H;
   const int rank = (int)cluster.block_rank();
-  setup_tables<F, NC>(p, rank, true);
+  setup_tables<F, S, NC, T>(p, rank, true);
   __syncthreads();
 
   const int cid = blockIdx.x / C;
@@ -458,26 +572,42 @@ __global__ void __launch_bounds__(kThreads, 1) correlate_kernel(PlanDev p, Corre
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
+    if constexpr (F == 4096) {
+      // S2: forward passes 1-2; S2-S5 fused: forward pass 3, the product
+      // Y = conj(Z) A + Z' B with sum |Y|^2, inverse pass 1; S5: passes 2-3
+      fwd_first_pass<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold);
+      stockham_pass<F, NC, T, 16, 16, false>(SM::cols(), SM::tw2());
+      fused_mid<S, NC, T>(rank, a.AB, SM::red());
+      if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
+        *SM::sigpart() = s;
+      }
+      __syncthreads();
+      stockham_pass<F, NC, T, 16, 16, true>(SM::cols(), SM::tw2());
+      inv_last_pass<F, S, NC, T>();
+    } else {
     // S2: template spectrum (column FFTs of the packed, twiddled template)
-    forward_columns<F, NC>(S, a.bank + k * a.Lp, nz, nfold);
+    forward_columns<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold);
 
     // S3 + S4: Y = conj(Z) A + Z' B over this CTA's bin pairs, sum |Y|^2
     float acc = 0.f;
 #pragma unroll
     for (int ui = 0; ui < UPC; ++ui) {
       const int ug = rank * UPC + ui;
-      const int count = unit_items<F>(S, ug);
-      for (int it = threadIdx.x; it < count; it += kThreads) {
-        const PairItem q = pair_item<F>(S, ug, ui, it);
+      const int count = unit_items<F, S>(ug);
+#pragma unroll 2
+      for (int it = threadIdx.x; it < count; it += T) {
+        const PairItem q = pair_item<F, S>(ug, ui, it);
         float2* cj = SM::col(q.sj) + pad(q.a);
         float2* cp = SM::col(q.sp) + pad(q.ap);
-        const float2 zj = *cj, zp = *cp;
         const float4 abj = __ldcg(a.AB + q.b * F + q.a);
+        const float4 abp = __ldcg(a.AB + q.bp * F + q.ap);
+        const float2 zj = *cj, zp = *cp;
         const float2 yj = cadd(cconjmul(zj, make_float2(abj.x, abj.y)),
                                cmul(zp, make_float2(abj.z, abj.w)));
         acc = fmaf(yj.x, yj.x, fmaf(yj.y, yj.y, acc));
         if (cj != cp) {
-          const float4 abp = __ldcg(a.AB + q.bp * F + q.ap);
           const float2 yp = cadd(cconjmul(zp, make_float2(abp.x, abp.y)),
                                  cmul(zj, make_float2(abp.z, abp.w)));
           acc = fmaf(yp.x, yp.x, fmaf(yp.y, yp.y, acc));
@@ -491,16 +621,18 @@ __global__ void __launch_bounds__(kThreads, 1) correlate_kernel(PlanDev p, Corre
     __syncthreads();
     if (threadIdx.x == 0) {
       float s = 0.f;
-      for (int w = 0; w < kThreads / 32; ++w) s += SM::red()[w];
+      for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
       *SM::sigpart() = s;
     }
 
     // S5: inverse column FFTs (the first pass reads after the barrier above)
-    inverse_columns<F, NC>(S);
+    inverse_columns<F, S, NC, T>();
+    }
 
     cluster.sync();  // every column and every sigma partial of the cluster is ready
 
     float tot = 0.f;
+#pragma unroll
     for (int q = 0; q < C; ++q) tot += *cluster.map_shared_rank(SM::sigpart(), (unsigned)q);
     const float sigma = sqrtf(2.0f * tot) / (float)N;
     const float thr = a.kappa * sigma;
@@ -508,109 +640,36 @@ __global__ void __launch_bounds__(kThreads, 1) correlate_kernel(PlanDev p, Corre
     if (rank == 0 && threadIdx.x == 0) a.sigma[krow] = sigma;
 
     // S6: S-point combine, threshold, warp-ballot compaction
-    if constexpr (NC == 1) {
-      combine_and_emit<F, NC, 1>(C, H, rank, thr, (uint32_t)k, krow, a);
-    } else if constexpr (NC == 2) {
-      combine_and_emit<F, NC, 2>(C, H, rank, thr, (uint32_t)k, krow, a);
-    } else {
-      switch (S) {
-        case 4: combine_and_emit<F, NC, 4>(C, H, rank, thr, (uint32_t)k, krow, a); break;
-        case 8: combine_and_emit<F, NC, 8>(C, H, rank, thr, (uint32_t)k, krow, a); break;
-        default: combine_and_emit<F, NC, 16>(C, H, rank, thr, (uint32_t)k, krow, a); break;
-      }
-    }
+    combine_and_emit<F, S, NC, T>(H, rank, thr, (uint32_t)k, krow, a);
 
     cluster.sync();  // remote reads done before the columns are overwritten
   }
 }
 
 // ---------------------------------------------------------------------------
-// Bank synthesis: w[m] = T(m) sin(2 pi phase(m)), unit L2 norm
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double chirp_sample(unsigned long long alpha, unsigned long long beta,
-                                               int64_t m, int64_t L, int width, double denom) {
-  const unsigned long long um = (unsigned long long)m;
-  // phase in cycles * 2^64, exact modulo one cycle
-  const unsigned long long ph = alpha * um + beta * (um * um);
-  const double c = (double)(long long)ph * 0x1p-64;  // in [-1/2, 1/2)
-  const double s = sinpi(2.0 * c);
-  const int64_t mm = m < L - 1 - m ? m : L - 1 - m;
-  double t = 1.0;
-  if (mm <= width) t = 0.5 * (1.0 - cospi(2.0 * (double)mm / denom));
-  return t * s;
-}
-
-__global__ void __launch_bounds__(256) bank_chirp_kernel(const unsigned long long* __restrict__ ab,
-                                                         int64_t L, int64_t Lp, double frac,
-                                                         float* __restrict__ bank) {
-  __shared__ double red[8];
-  const int64_t k = blockIdx.x;
-  const unsigned long long alpha = ab[2 * k], beta = ab[2 * k + 1];
-  const int width = (frac > 0.0 && L >= 2) ? (int)floor(frac * (double)(L - 1) / 2.0) : -1;
-  const double denom = frac * (double)(L - 1);
-  double acc = 0.0;
-  for (int64_t m = threadIdx.x; m < L; m += blockDim.x) {
-    const double v = chirp_sample(alpha, beta, m, L, width, denom);
-    acc = fma(v, v, acc);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  double norm = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) norm += red[w];
-  const double scale = norm > 0.0 ? 1.0 / sqrt(norm) : 0.0;
-  float* row = bank + k * Lp;
-  for (int64_t m = threadIdx.x; m < Lp; m += blockDim.x)
-    row[m] = m < L ? (float)(chirp_sample(alpha, beta, m, L, width, denom) * scale) : 0.f;
-}
-
-// ---------------------------------------------------------------------------
-// Launchers
+// Launch helpers
 // ---------------------------------------------------------------------------
 template <typename K>
 static cudaError_t ensure_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int F, int NC>
-static cudaError_t launch_segment_t(const PlanDev& p, const float* y, float2* D, float4* AB,
-                                    cudaStream_t s) {
-  constexpr size_t smem = smem_bytes<F, NC>();
-  cudaError_t e = ensure_smem(segment_kernel<F, NC>, smem);
-  if (e != cudaSuccess) return e;
-  segment_kernel<F, NC><<<p.g.C, kThreads, smem, s>>>(p, y, D, AB);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_segment(const PlanDev& p, const float* y, float2* D, float4* AB,
-                           cudaStream_t s) {
-  const Geometry& g = p.g;
-  if (g.F == 4096) {
-    if (g.NC == 4) return launch_segment_t<4096, 4>(p, y, D, AB, s);
-    if (g.NC == 2) return launch_segment_t<4096, 2>(p, y, D, AB, s);
-    return launch_segment_t<4096, 1>(p, y, D, AB, s);
-  }
-  if (g.F == 2048) return launch_segment_t<2048, 1>(p, y, D, AB, s);
-  if (g.F == 1024) return launch_segment_t<1024, 1>(p, y, D, AB, s);
-  if (g.F == 512) return launch_segment_t<512, 1>(p, y, D, AB, s);
-  return cudaErrorInvalidValue;
-}
-
-template <int F, int NC>
-static cudaError_t launch_correlate_t(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
-  constexpr size_t smem = smem_bytes<F, NC>();
-  cudaError_t e = ensure_smem(correlate_kernel<F, NC>, smem);
+template <int F, int S, int NC, int T, int MINB, bool HALFZ>
+static cudaError_t launch_corr_t(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
+  constexpr int C = ColMap<S, NC>::C;
+  constexpr size_t smem = Lay<F, NC>::total;
+  auto kern = correlate_kernel<F, S, NC, T, MINB, HALFZ>;
+  cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)p.g.C;
+  attr[0].val.clusterDim.x = (unsigned)C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.blockDim = dim3(T, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   int dev = 0, sms = 0;
@@ -618,36 +677,26 @@ static cudaError_t launch_correlate_t(const PlanDev& p, const CorrelateArgs& a, 
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  cfg.gridDim = dim3((unsigned)(sms / p.g.C * p.g.C), 1, 1);
+  cfg.gridDim = dim3((unsigned)(sms / C * C * MINB), 1, 1);
   int max_clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&max_clusters, correlate_kernel<F, NC>, &cfg);
+  e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
   if (e != cudaSuccess) return e;
   if (max_clusters < 1) return cudaErrorInvalidConfiguration;
   int64_t want = a.k1 - a.k0;
   if (a.max_clusters > 0 && want > a.max_clusters) want = a.max_clusters;
   if (want > max_clusters) want = max_clusters;
-  cfg.gridDim = dim3((unsigned)(want * p.g.C), 1, 1);
-  return cudaLaunchKernelEx(&cfg, correlate_kernel<F, NC>, p, a);
+  cfg.gridDim = dim3((unsigned)(want * C), 1, 1);
+  return cudaLaunchKernelEx(&cfg, kern, p, a);
 }
 
-cudaError_t launch_correlate(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
-  if (a.k1 <= a.k0) return cudaSuccess;
-  const Geometry& g = p.g;
-  if (g.F == 4096) {
-    if (g.NC == 4) return launch_correlate_t<4096, 4>(p, a, s);
-    if (g.NC == 2) return launch_correlate_t<4096, 2>(p, a, s);
-    return launch_correlate_t<4096, 1>(p, a, s);
-  }
-  if (g.F == 2048) return launch_correlate_t<2048, 1>(p, a, s);
-  if (g.F == 1024) return launch_correlate_t<1024, 1>(p, a, s);
-  if (g.F == 512) return launch_correlate_t<512, 1>(p, a, s);
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_bank_chirp(const unsigned long long* alpha_beta, int64_t count, int64_t L,
-                              int64_t Lp, double taper_frac, float* bank, cudaStream_t s) {
-  if (count <= 0) return cudaSuccess;
-  bank_chirp_kernel<<<(unsigned)count, 256, 0, s>>>(alpha_beta, L, Lp, taper_frac, bank);
+template <int F, int S, int NC, int T>
+static cudaError_t launch_segment_t(const PlanDev& p, const float* y, float2* D, float4* AB,
+                                    cudaStream_t s) {
+  constexpr size_t smem = Lay<F, NC>::total;
+  auto kern = segment_kernel<F, S, NC, T>;
+  cudaError_t e = ensure_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<ColMap<S, NC>::C, T, smem, s>>>(p, y, D, AB);
   return cudaGetLastError();
 }
 

@@ -7,8 +7,6 @@
 
 namespace bege {
 
-constexpr int kThreads = 512;  // threads per CTA of every column kernel
-
 // Shared-memory index with one padding slot every 16 complex values: keeps
 // the strided Stockham stores (stride 16 and 17*16) free of bank conflicts.
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
@@ -82,11 +80,23 @@ __device__ __forceinline__ void dft8(float2 (&x)[8]) {
 }
 
 // 16 = 4 x 4: DFT4 over the stride-4 index, twiddle w16^(n2 k1), DFT4 over
-// the offset index, then transpose to natural order.
-template <bool INV>
+// the offset index, then transpose to natural order.  HALFZ: inputs 8..15
+// are known to be zero (a zero-padded half), which shortens the first DFT4s.
+template <bool INV, bool HALFZ = false>
 __device__ __forceinline__ void dft16(float2 (&x)[16]) {
 #pragma unroll
-  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(x[n2], x[n2 + 4], x[n2 + 8], x[n2 + 12]);
+  for (int n2 = 0; n2 < 4; ++n2) {
+    if constexpr (HALFZ) {
+      const float2 a = x[n2], b = x[n2 + 4];
+      const float2 mb = mul_mi<INV>(b);
+      x[n2] = cadd(a, b);
+      x[n2 + 8] = csub(a, b);
+      x[n2 + 4] = cadd(a, mb);
+      x[n2 + 12] = csub(a, mb);
+    } else {
+      dft4<INV>(x[n2], x[n2 + 4], x[n2 + 8], x[n2 + 12]);
+    }
+  }
   // x[n2 + 4 k1] *= w16^(n2 k1)
   x[5] = twc<INV>(x[5], kC1, kS1);     // m = 1
   x[6] = twc<INV>(x[6], kR2, kR2);     // m = 2
@@ -108,8 +118,9 @@ __device__ __forceinline__ void dft16(float2 (&x)[16]) {
   for (int i = 0; i < 16; ++i) x[i] = t[i];
 }
 
-template <int R, bool INV>
+template <int R, bool INV, bool HALFZ = false>
 __device__ __forceinline__ void dft(float2 (&x)[R]) {
+  static_assert(!HALFZ || R == 16, "half-zero DFT only for radix 16");
   if constexpr (R == 1) {
   } else if constexpr (R == 2) {
     dft2<INV>(x[0], x[1]);
@@ -119,49 +130,68 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
     dft8<INV>(x);
   } else {
     static_assert(R == 16, "radix");
-    dft16<INV>(x);
+    dft16<INV, HALFZ>(x);
   }
 }
 
-// One in-place Stockham pass of radix R over nc columns of length F in
+// One in-place Stockham pass of radix R over NC columns of length F in
 // shared memory (column c at cols + c * col_stride<F>(), padded indexing).
-// Butterfly j reads col[j + r F/R], twiddles by w(Ns R)^(k r) with
-// k = j mod Ns (table tw[r*Ns + k]), and writes col[(j-k) R + k + r Ns].
-// Butterflies are taken in rounds of kThreads; since F/R divides kThreads
-// every round covers whole columns, so a round can load, synchronise and
-// store without touching the columns of the next round.  Each thread holds
-// one butterfly (R complex values) across a barrier.
-template <int F, int R, bool INV>
-__device__ __forceinline__ void stockham_pass(float2* cols, int nc, int Ns, const float2* tw) {
+// Butterfly j reads col[j + r F/R], twiddles by w(NS R)^(k r) with
+// k = j mod NS (table tw[r*NS + k]), and writes col[(j-k) R + k + r NS].
+// Butterflies are taken in rounds of T threads; since F/R divides T every
+// round covers whole columns, so a round can load, synchronise and store
+// without touching the columns of the next round.  Each thread holds one
+// butterfly (R complex values) across a barrier: holding two (one round)
+// costs fewer barriers but spills at 128 registers and measured slower.
+// With F/R and NS multiples of 16 the padded addresses of a butterfly are
+// one base plus constants.
+template <int F, int NC, int T, int R, int NS, bool INV>
+__device__ __forceinline__ void stockham_pass(float2* cols, const float2* tw) {
   constexpr int NB = F / R;
-  static_assert(kThreads % NB == 0, "rounds must cover whole columns");
-  const int total = nc * NB;
-  const int rounds = (total + kThreads - 1) / kThreads;
+  static_assert(T % NB == 0, "rounds must cover whole columns");
+  constexpr int total = NC * NB;
+  constexpr int rounds = (total + T - 1) / T;
+  constexpr int CS = col_stride<F>();
+#pragma unroll
   for (int i = 0; i < rounds; ++i) {
-    const int idx = threadIdx.x + i * kThreads;
-    const bool act = idx < total;
+    const int idx = threadIdx.x + i * T;
+    const bool act = (total % T == 0) || idx < total;
     const int c = idx / NB, j = idx - c * NB;
-    const int k = j & (Ns - 1);
+    const int k = j & (NS - 1);
     float2 v[R];
     if (act) {
-      const float2* col = cols + c * col_stride<F>();
+      const float2* col = cols + c * CS;
+      if constexpr (NB % 16 == 0) {
+        const float2* p = col + pad(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = col[pad(j + r * NB)];
-      if (Ns > 1) {
+        for (int r = 0; r < R; ++r) v[r] = p[r * (NB + NB / 16)];
+      } else {
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const float2 t = tw[r * Ns + k];
-          v[r] = INV ? cmulc(v[r], t) : cmul(v[r], t);
-        }
+        for (int r = 0; r < R; ++r) v[r] = col[pad(j + r * NB)];
+      }
+      if constexpr (NS > 1) {
+        const float2* t = tw + k;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = INV ? cmulc(v[r], t[r * NS]) : cmul(v[r], t[r * NS]);
       }
       dft<R, INV>(v);
     }
     __syncthreads();
     if (act) {
-      float2* col = cols + c * col_stride<F>();
+      float2* col = cols + c * CS;
       const int base = (j - k) * R + k;
+      if constexpr (NS % 16 == 0) {
+        float2* p = col + pad(base);
 #pragma unroll
-      for (int r = 0; r < R; ++r) col[pad(base + r * Ns)] = v[r];
+        for (int r = 0; r < R; ++r) p[r * (NS + NS / 16)] = v[r];
+      } else if constexpr (NS == 1 && R == 16) {
+        float2* p = col + pad(base);
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r] = v[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) col[pad(base + r * NS)] = v[r];
+      }
     }
   }
   __syncthreads();

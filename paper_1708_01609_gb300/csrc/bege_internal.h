@@ -17,8 +17,8 @@ namespace bege {
 // "column" b, an F-point FFT of a twiddled, folded input (a four-step whose
 // first step is pruned by the template's support).  Columns b and S-b hold
 // the bins j and H-j that the real-FFT unpacking couples, so they form a
-// "unit" processed by one CTA; the C CTAs of a thread-block cluster share
-// the S columns and exchange them through distributed shared memory only for
+// "unit" processed by one CTA; the CTAs of a thread-block cluster share the
+// S columns and exchange them through distributed shared memory only for
 // the final S-point combine.
 struct Geometry {
   int N;    // real samples
@@ -26,9 +26,14 @@ struct Geometry {
   int F;    // column FFT length (512..4096)
   int S;    // columns = H / F (1..16)
   int R0;   // radix of the first Stockham pass = F / 256
-  int C;    // CTAs per cluster
-  int NC;   // columns per CTA
-  int UPC;  // units per CTA
+};
+
+// Launch shape of the correlate kernel: columns per CTA (the cluster has
+// S / nc CTAs) and threads per CTA.  Chosen per N by default or by the
+// autotuner.
+struct CorrConfig {
+  int nc;
+  int threads;
 };
 
 // Device twiddle tables for one N (computed in FP64 on the host, rounded to
@@ -46,8 +51,10 @@ struct PlanDev {
 
 Geometry make_geometry(int64_t n);
 
-// Shared-memory bytes of the correlate / segment kernels for geometry g.
-size_t correlate_smem_bytes(const Geometry& g);
+// Launch shapes compiled for geometry g (at most `max`); returns the count.
+int correlate_configs(const Geometry& g, CorrConfig* out, int max);
+CorrConfig default_config(const Geometry& g);
+bool config_valid(const Geometry& g, CorrConfig c);
 
 // S1: segment spectrum.  y: N floats (device).  D: H+1 complex (natural
 // order).  AB: S*F float4 {A_j, B_j} in residue-major order [b*F + a].
@@ -70,7 +77,20 @@ struct CorrelateArgs {
   float* dump;
   int max_clusters;  // 0 = as many as fit
 };
-cudaError_t launch_correlate(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s);
+cudaError_t launch_correlate(const PlanDev& p, const CorrelateArgs& a, CorrConfig cfg,
+                             cudaStream_t s);
+
+// Per-S launchers (one translation unit each); halfz: Lp <= F.
+cudaError_t launch_correlate_s1(const PlanDev& p, const CorrelateArgs& a, CorrConfig c, bool halfz,
+                                cudaStream_t s);
+cudaError_t launch_correlate_s2(const PlanDev& p, const CorrelateArgs& a, CorrConfig c, bool halfz,
+                                cudaStream_t s);
+cudaError_t launch_correlate_s4(const PlanDev& p, const CorrelateArgs& a, CorrConfig c, bool halfz,
+                                cudaStream_t s);
+cudaError_t launch_correlate_s8(const PlanDev& p, const CorrelateArgs& a, CorrConfig c, bool halfz,
+                                cudaStream_t s);
+cudaError_t launch_correlate_s16(const PlanDev& p, const CorrelateArgs& a, CorrConfig c, bool halfz,
+                                 cudaStream_t s);
 
 // Bank synthesis: count chirps, phase coefficients alpha/beta as unsigned
 // 64-bit fixed point (cycles * 2^64), L samples, taper fraction; rows of Lp.

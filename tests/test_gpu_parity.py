@@ -299,3 +299,33 @@ def test_budget_refusal():
         c.bege_define_bank_samples(np.ones((1000, 4096), np.float32))
     assert e.value.code == -3
     c.close()
+
+
+@pytest.mark.parametrize("n", [1 << 14, 1 << 15, 1 << 16, 1 << 17])
+def test_every_launch_shape_matches_oracle(ctx, n):
+    """Every compiled launch shape (columns per CTA, threads per CTA) gives
+    the same correlation (bitwise: each column FFT does identical arithmetic)
+    and sigma within 1e-6 of the oracle; the autotuner picks one of them."""
+    y = S.band_limited_noise(n, 21)
+    bank = S.random_samples_bank(5, 4096, 22)
+    seg = ctx.bege_load_segment(y)
+    bid = ctx.bege_define_bank_samples(bank)
+    rho, sig = oracle_rho(y, bank.astype(np.float64))
+    shapes = ctx.bege_list_configs(n)
+    assert len(shapes) >= 1
+    dumps = []
+    for nc, threads in shapes:
+        ctx.bege_set_config(n, nc, threads)
+        assert ctx.bege_get_config(n) == (nc, threads)
+        d = ctx.bege_dump_correlation(seg, bid, 0, 5)
+        assert np.all(np.max(np.abs(d - rho), axis=1) / sig <= TOL_FP32)
+        job = ctx.bege_correlate(seg, bid, 0, 5, 4.0)
+        assert np.all(np.abs(ctx.bege_get_sigma(job, 5) / sig - 1) <= 1e-6)
+        ctx.bege_release(job)
+        dumps.append(d)
+    for d in dumps[1:]:
+        assert np.array_equal(d, dumps[0])
+    best = ctx.bege_autotune(seg, bid, 0, 5, reps=1)
+    assert best > 0 and ctx.bege_get_config(n) in shapes
+    for h in (bid, seg):
+        ctx.bege_release(h)
