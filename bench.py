@@ -320,12 +320,68 @@ def run_ours(args):
     return 0
 
 
+def run_batch_form(args):
+    """Batching form: 64 segments, N uniform over 2^14..2^17, each against
+    its own sub-bank of 2^12..2^16 chirps (tau 0.5 s or 1 s), 8 injections
+    each; one persistent launch in a CUDA graph per step, plan chosen by the
+    batch autotuner."""
+    import torch
+    from paper_1708_01609_gb300 import binding, build
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    build()
+    ctx = binding.Context(0, tail_capacity=1 << 22)
+    entries, grids = S.batch_case()
+    stream_obj = torch.cuda.current_stream()
+    stream = stream_obj.cuda_stream
+    banks = {tau: ctx.bege_define_bank(grids[tau], tau=tau, taper_frac=0.05, stream=stream)
+             for tau in grids}
+    spec = [(e.seg.y, banks[e.tau], e.k0, e.k1, KAPPA) for e in entries]
+    batch = ctx.bege_batch_create(spec, stream=stream)
+    tuned_ms = ctx.bege_batch_autotune(batch, reps=2, stream=stream)
+    plan = ctx.bege_batch_get_plan(batch)
+    for _ in range(args.warmup):
+        ctx.bege_batch_run(batch, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream_obj)
+    for _ in range(args.steps):
+        ctx.bege_batch_run(batch, stream)
+    e1.record(stream_obj)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    corr = sum(e.k1 - e.k0 for e in entries)
+    flops = sum((e.k1 - e.k0) * metrics.nominal_flops_per_correlation(e.seg.n) for e in entries)
+    tails = sum(ctx.bege_batch_fetch_tails(batch, i, capacity=0)[1] for i in range(len(entries)))
+    line = {
+        "form": "batch", "metric": "chirp correlations/s, batching form", "value":
+        corr * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": (f"{len(entries)} segments, N uniform over 2^14..2^17, sub-banks "
+                                "of 2^12..2^16 chirps (log-uniform), tau 0.5 or 1 s, 8 injections "
+                                "each, kappa 5.5"),
+                   "correlations_per_step": corr,
+                   "segment_lengths": sorted({e.seg.n for e in entries})},
+        "nominal_tflops": flops * args.steps / (ms / 1e3) / 1e12,
+        "plan": {"plan": ["persistent", "per-segment"][plan[0]], "chunk": plan[1],
+                 "order": ["longest-first", "interleaved"][plan[2]], "autotuned_ms": tuned_ms},
+        "tails_per_step": tails,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["search", "batch"], default="search",
+                    help="search: the headline N=2^16 x 2^20 step; batch: the batching form")
     ap.add_argument("--templates", type=int, default=1 << 20,
                     help="bank rows per step (the benchmark uses all 2^20)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -335,6 +391,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "batch":
+        return run_batch_form(args)
     return run_ours(args)
 
 

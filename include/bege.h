@@ -177,8 +177,65 @@ int bege_get_config(bege_ctx* ctx, int64_t n, int32_t* nc, int32_t* threads);
 int bege_autotune(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin, int64_t k_end,
                   int32_t reps, void* stream, float* best_ms);
 
-/* Release a segment, bank or job handle and its device memory (job buffers
- * return to the context's pool).  Errors: EINVAL for an unknown handle. */
+/* ---- Batching form ------------------------------------------------------
+ * Many segments of different lengths, each against its own bank range, in
+ * one persistent kernel launch captured with the batched segment-spectrum
+ * kernel in a CUDA graph (Sec. 3.2: batch mode over blocks of segments and
+ * groups of templates).  n must be one of 2^14, 2^15, 2^16, 2^17 and the
+ * bank's template length at most 4096 samples (tau <= 1 s at 4096 Hz). */
+typedef struct {
+  const float* strain;   /* HOST pointer to n FP32 samples (copied at creation) */
+  int64_t n;
+  int32_t bank_id;
+  int32_t reserved;      /* must be 0 */
+  int64_t k_begin;       /* bank rows [k_begin, k_end) */
+  int64_t k_end;
+  float kappa;
+  float reserved2;       /* must be 0 */
+} bege_batch_entry;
+
+/* Create a batch: copies the strains to the device, allocates per-entry
+ * sigma and tail buffers (`tail_capacity` records per entry, 0 = the
+ * context default) and captures the graph.  *batch_id receives the handle
+ * (released with bege_release).  Errors: EINVAL, EBUDGET, ENOMEM, ECUDA. */
+int bege_batch_create(bege_ctx* ctx, const bege_batch_entry* entries, int32_t count,
+                      uint64_t tail_capacity, void* stream, int32_t* batch_id);
+
+/* Launch the batch's graph on `stream` (asynchronous): segment spectra of
+ * every entry, then all correlations.  Each run overwrites the previous
+ * run's results. */
+int bege_batch_run(bege_ctx* ctx, int32_t batch_id, void* stream);
+
+/* Wait for the last run and report its device time (CUDA events around the
+ * graph launch) in milliseconds. */
+int bege_batch_elapsed_ms(bege_ctx* ctx, int32_t batch_id, float* ms);
+
+/* Wait for the last run and copy entry `entry`'s tails / sigma to HOST
+ * memory; same conventions as bege_fetch_tails / bege_get_sigma. */
+int bege_batch_fetch_tails(bege_ctx* ctx, int32_t batch_id, int32_t entry, bege_tail* out,
+                           int64_t capacity, int64_t* n_written, int64_t* n_total);
+int bege_batch_get_sigma(bege_ctx* ctx, int32_t batch_id, int32_t entry, float* out,
+                         int64_t count);
+
+/* Execution plan of a batch.  plan 0: the persistent kernel (clusters of 8
+ * CTAs taking work items of `chunk` templates from a queue; `order` 0 =
+ * longest segments first, 1 = entries interleaved); plan 1: one launch per
+ * entry with the per-length launch shape of bege_set_config. */
+int bege_batch_set_plan(bege_ctx* ctx, int32_t batch_id, int32_t plan, int64_t chunk,
+                        int32_t order);
+int bege_batch_get_plan(bege_ctx* ctx, int32_t batch_id, int32_t* plan, int64_t* chunk,
+                        int32_t* order);
+
+/* Autotuner of the batching form: times every plan (plan 0 over chunks of
+ * 64..2048 templates and both orders, plan 1 with the current per-length
+ * shapes) with `reps` runs each after one warm-up, keeps the fastest and
+ * reports its median time in *best_ms.  Synchronous on `stream`. */
+int bege_batch_autotune(bege_ctx* ctx, int32_t batch_id, int32_t reps, void* stream,
+                        float* best_ms);
+
+/* Release a segment, bank, job or batch handle and its device memory (job
+ * buffers return to the context's pool).  Errors: EINVAL for an unknown
+ * handle. */
 int bege_release(bege_ctx* ctx, int32_t handle);
 
 /* Message of the last error on the calling thread ("" if none).  ctx may be

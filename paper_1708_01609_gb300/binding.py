@@ -45,6 +45,12 @@ class bege_chirp(ctypes.Structure):
     _fields_ = [("f0", ctypes.c_double), ("fdot", ctypes.c_double)]
 
 
+class bege_batch_entry(ctypes.Structure):
+    _fields_ = [("strain", ctypes.c_void_p), ("n", ctypes.c_int64), ("bank_id", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("k_begin", ctypes.c_int64), ("k_end", ctypes.c_int64),
+                ("kappa", ctypes.c_float), ("reserved2", ctypes.c_float)]
+
+
 class bege_tail(ctypes.Structure):
     _fields_ = [("tmpl", ctypes.c_uint32), ("lag", ctypes.c_uint32), ("value", ctypes.c_float)]
 
@@ -81,6 +87,14 @@ SIGNATURES = {
     "bege_get_config": (ctypes.c_int, [_VP, _I64, _PI32, _PI32]),
     "bege_autotune": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, _I32, _VP,
                                      ctypes.POINTER(ctypes.c_float)]),
+    "bege_batch_create": (ctypes.c_int, [_VP, _VP, _I32, ctypes.c_uint64, _VP, _PI32]),
+    "bege_batch_run": (ctypes.c_int, [_VP, _I32, _VP]),
+    "bege_batch_elapsed_ms": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_float)]),
+    "bege_batch_fetch_tails": (ctypes.c_int, [_VP, _I32, _I32, _VP, _I64, _PI64, _PI64]),
+    "bege_batch_get_sigma": (ctypes.c_int, [_VP, _I32, _I32, _VP, _I64]),
+    "bege_batch_set_plan": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I32]),
+    "bege_batch_get_plan": (ctypes.c_int, [_VP, _I32, _PI32, _PI64, _PI32]),
+    "bege_batch_autotune": (ctypes.c_int, [_VP, _I32, _I32, _VP, ctypes.POINTER(ctypes.c_float)]),
     "bege_release": (ctypes.c_int, [_VP, _I32]),
     "bege_last_error": (ctypes.c_char_p, [_VP]),
     "bege_version": (ctypes.c_char_p, []),
@@ -266,6 +280,62 @@ class Context:
         ms = ctypes.c_float()
         _check(self.lib.bege_autotune(self.h, seg, bank, k_begin, k_end, reps, stream,
                                       ctypes.byref(ms)), "bege_autotune")
+        return float(ms.value)
+
+    # -- batching form ----------------------------------------------------
+    def bege_batch_create(self, entries, tail_capacity: int = 0, stream: int = 0) -> int:
+        """entries: list of (strain FP32 array, bank_id, k_begin, k_end, kappa)."""
+        keep = [np.ascontiguousarray(e[0], dtype=np.float32) for e in entries]
+        arr = (bege_batch_entry * len(entries))()
+        for i, (e, y) in enumerate(zip(entries, keep)):
+            arr[i] = bege_batch_entry(y.ctypes.data, len(y), e[1], 0, e[2], e[3], e[4], 0.0)
+        bid = _I32()
+        _check(self.lib.bege_batch_create(self.h, arr, len(entries), tail_capacity, stream,
+                                          ctypes.byref(bid)), "bege_batch_create")
+        return bid.value
+
+    def bege_batch_run(self, batch: int, stream: int = 0) -> None:
+        _check(self.lib.bege_batch_run(self.h, batch, stream), "bege_batch_run")
+
+    def bege_batch_elapsed_ms(self, batch: int) -> float:
+        ms = ctypes.c_float()
+        _check(self.lib.bege_batch_elapsed_ms(self.h, batch, ctypes.byref(ms)),
+               "bege_batch_elapsed_ms")
+        return float(ms.value)
+
+    def bege_batch_fetch_tails(self, batch: int, entry: int, capacity: int | None = None):
+        nw, nt = _I64(), _I64()
+        if capacity is None:
+            _check(self.lib.bege_batch_fetch_tails(self.h, batch, entry, None, 0, ctypes.byref(nw),
+                                                   ctypes.byref(nt)), "bege_batch_fetch_tails",
+                   ok=(BEGE_OK, BEGE_EOVERFLOW))
+            capacity = nt.value
+        out = np.empty(capacity, dtype=TAIL_DTYPE)
+        _check(self.lib.bege_batch_fetch_tails(self.h, batch, entry, _ptr(out), capacity,
+                                               ctypes.byref(nw), ctypes.byref(nt)),
+               "bege_batch_fetch_tails", ok=(BEGE_OK, BEGE_EOVERFLOW))
+        return out[: nw.value], nt.value
+
+    def bege_batch_get_sigma(self, batch: int, entry: int, count: int) -> np.ndarray:
+        out = np.empty(count, dtype=np.float32)
+        _check(self.lib.bege_batch_get_sigma(self.h, batch, entry, _ptr(out), count),
+               "bege_batch_get_sigma")
+        return out
+
+    def bege_batch_set_plan(self, batch: int, plan: int, chunk: int = 256, order: int = 0):
+        _check(self.lib.bege_batch_set_plan(self.h, batch, plan, chunk, order),
+               "bege_batch_set_plan")
+
+    def bege_batch_get_plan(self, batch: int) -> tuple[int, int, int]:
+        p, c, o = _I32(), _I64(), _I32()
+        _check(self.lib.bege_batch_get_plan(self.h, batch, ctypes.byref(p), ctypes.byref(c),
+                                            ctypes.byref(o)), "bege_batch_get_plan")
+        return p.value, c.value, o.value
+
+    def bege_batch_autotune(self, batch: int, reps: int = 2, stream: int = 0) -> float:
+        ms = ctypes.c_float()
+        _check(self.lib.bege_batch_autotune(self.h, batch, reps, stream, ctypes.byref(ms)),
+               "bege_batch_autotune")
         return float(ms.value)
 
     def bege_release(self, handle: int) -> None:

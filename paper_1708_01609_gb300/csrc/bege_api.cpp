@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "bege_batch.h"
 #include "bege_internal.h"
 
 namespace {
@@ -91,6 +92,30 @@ static void destroy_job_events(Job* j) {
   j->done = j->k_start = j->k_stop = nullptr;
 }
 
+struct BatchEntryHost {
+  int64_t n = 0;
+  int32_t bank = -1;
+  int64_t k0 = 0, k1 = 0;
+  float kappa = 0.f;
+};
+
+struct Batch {
+  std::vector<BatchEntryHost> entries;
+  std::vector<bege::BatchSeg> segs_host;
+  DevBuf y, D, AB, segs, items, jobs, queue, sigma, recs, counters;
+  std::vector<size_t> sigma_off;  // per entry, in floats
+  uint64_t cap = 0;               // tail records per entry
+  int n_items = 0, n_jobs = 0;
+  int32_t plan = 0, order = 0;
+  int64_t chunk = 256;
+  bege::BatchArgs args{};
+  cudaStream_t cs = nullptr;      // capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr, t0 = nullptr, t1 = nullptr;
+  bool ran = false;
+};
+
 struct bege_ctx {
   int device = 0;
   bege_config cfg{};
@@ -101,6 +126,7 @@ struct bege_ctx {
   std::map<int32_t, std::unique_ptr<Segment>> segs;
   std::map<int32_t, std::unique_ptr<Bank>> banks;
   std::map<int32_t, std::unique_ptr<Job>> jobs;
+  std::map<int32_t, std::unique_ptr<Batch>> batches;
   std::vector<std::unique_ptr<JobBuffers>> pool;
   std::map<int64_t, bege::CorrConfig> configs;  // chosen launch shape per N
 
@@ -277,6 +303,165 @@ Job* find_job(bege_ctx* ctx, int32_t id) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Batching form
+// ---------------------------------------------------------------------------
+static void destroy_batch(bege_ctx* ctx, Batch* b) {
+  if (b->done) cudaEventSynchronize(b->done);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->t0) cudaEventDestroy(b->t0);
+  if (b->t1) cudaEventDestroy(b->t1);
+  if (b->cs) cudaStreamDestroy(b->cs);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->done = b->t0 = b->t1 = nullptr;
+  b->cs = nullptr;
+  for (DevBuf* d : {&b->y, &b->D, &b->AB, &b->segs, &b->items, &b->jobs, &b->queue, &b->sigma,
+                    &b->recs, &b->counters})
+    ctx->release(d);
+}
+
+static int log2i(int64_t n) {
+  int k = 0;
+  while ((int64_t(1) << k) < n) ++k;
+  return k;
+}
+
+// Work items of `chunk` templates; order 0: longest segments first,
+// order 1: entries interleaved chunk by chunk.
+static std::vector<bege::BatchItem> batch_items(const Batch& b, int64_t chunk, int order) {
+  std::vector<std::vector<bege::BatchItem>> per(b.entries.size());
+  for (size_t e = 0; e < b.entries.size(); ++e)
+    for (int64_t k = b.entries[e].k0; k < b.entries[e].k1; k += chunk)
+      per[e].push_back({(int)e, 0, k, std::min(k + chunk, b.entries[e].k1)});
+  std::vector<bege::BatchItem> out;
+  if (order == 0) {
+    std::vector<size_t> idx(b.entries.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+      return b.entries[x].n > b.entries[y].n;
+    });
+    for (size_t i : idx) out.insert(out.end(), per[i].begin(), per[i].end());
+  } else {
+    for (size_t r = 0;; ++r) {
+      bool any = false;
+      for (auto& v : per)
+        if (r < v.size()) {
+          out.push_back(v[r]);
+          any = true;
+        }
+      if (!any) break;
+    }
+  }
+  return out;
+}
+
+// (Re)build the work items for the batch's plan and capture its graph.
+static int batch_build(bege_ctx* ctx, Batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (b->plan == 0) {
+    auto items = batch_items(*b, b->chunk, b->order);
+    if (b->items.bytes < items.size() * sizeof(bege::BatchItem)) {
+      ctx->release(&b->items);
+      int rc = ctx->alloc(&b->items, items.size() * sizeof(bege::BatchItem));
+      if (rc) return rc;
+    }
+    e = cudaMemcpy(b->items.ptr, items.data(), items.size() * sizeof(bege::BatchItem),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "batch items");
+    b->n_items = (int)items.size();
+    b->args.items = static_cast<const bege::BatchItem*>(b->items.ptr);
+    b->args.n_items = b->n_items;
+  }
+  const int clusters = bege::batch_max_clusters();
+  if (b->plan == 0 && clusters < 1) return fail(BEGE_ECUDA, "batch kernel does not fit");
+  // one uncaptured pass of the attribute setup of every kernel used below
+  if (b->plan == 1) {
+    for (const auto& en : b->entries) {
+      auto pl = ctx->plans[en.n];
+      auto ci = ctx->configs.find(en.n);
+      const bege::CorrConfig cc = ci != ctx->configs.end() ? ci->second : bege::default_config(pl->g);
+      bege::CorrelateArgs a{};
+      a.k0 = a.k1 = 0;  // empty range: returns before launching
+      bege::launch_correlate(pl->dev, a, cc, b->cs);
+    }
+  }
+  e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+  e = cudaMemsetAsync(b->counters.ptr, 0, b->counters.bytes, b->cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->queue.ptr, 0, b->queue.bytes, b->cs);
+  if (e == cudaSuccess)
+    e = bege::launch_segment_batch(b->args, static_cast<const bege::SegJob*>(b->jobs.ptr),
+                                   b->n_jobs, b->cs);
+  if (e == cudaSuccess) {
+    if (b->plan == 0) {
+      e = bege::launch_batch(b->args, std::min(clusters, b->n_items), b->cs);
+    } else {
+      for (size_t i = 0; i < b->entries.size() && e == cudaSuccess; ++i) {
+        const auto& en = b->entries[i];
+        const auto& sg = b->segs_host[i];
+        auto pl = ctx->plans[en.n];
+        auto ci = ctx->configs.find(en.n);
+        const bege::CorrConfig cc =
+            ci != ctx->configs.end() ? ci->second : bege::default_config(pl->g);
+        bege::CorrelateArgs a{};
+        a.AB = sg.AB;
+        a.bank = sg.bank;
+        a.Lp = sg.Lp;
+        a.k0 = sg.k0;
+        a.k1 = sg.k1;
+        a.kappa = sg.kappa;
+        a.sigma = sg.sigma;
+        a.recs = sg.recs;
+        a.cap = sg.cap;
+        a.counter = sg.counter;
+        a.dump = nullptr;
+        a.max_clusters = 0;
+        e = bege::launch_correlate(pl->dev, a, cc, b->cs);
+      }
+    }
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->cs, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return cuda_fail(e != cudaSuccess ? e : e2, "batch graph");
+  }
+  b->graph = g;
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+  return BEGE_OK;
+}
+
+static Batch* find_batch(bege_ctx* ctx, int32_t id) {
+  auto it = ctx->batches.find(id);
+  return it == ctx->batches.end() ? nullptr : it->second.get();
+}
+
+static int batch_wait(Batch* b) {
+  if (!b->ran) return fail(BEGE_ENOTREADY, "batch has not been run");
+  cudaError_t e = cudaEventSynchronize(b->done);
+  if (e != cudaSuccess) return cuda_fail(e, "batch");
+  return BEGE_OK;
+}
+
+static int batch_run_locked(Batch* b, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(b->t0, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(b->t1, s);
+  if (e == cudaSuccess) e = cudaEventRecord(b->done, s);
+  if (e != cudaSuccess) return cuda_fail(e, "batch run");
+  b->ran = true;
+  return BEGE_OK;
+}
+
 extern "C" {
 
 const char* bege_version(void) { return "bege 0.1 (sm_103a)"; }
@@ -331,6 +516,7 @@ int bege_destroy(bege_ctx* ctx) {
       ctx->release(&b->recs);
       ctx->release(&b->counter);
     }
+    for (auto& kv : ctx->batches) destroy_batch(ctx, kv.second.get());
     for (auto& kv : ctx->segs) {
       ctx->release(&kv.second->D);
       ctx->release(&kv.second->AB);
@@ -755,6 +941,260 @@ int64_t bege_bank_length(bege_ctx* ctx, int32_t bank_id) {
 
 uint64_t bege_device_bytes(const bege_ctx* ctx) { return ctx ? ctx->bytes : 0; }
 
+int bege_batch_create(bege_ctx* ctx, const bege_batch_entry* entries, int32_t count,
+                      uint64_t tail_capacity, void* stream, int32_t* batch_id) {
+  if (!ctx || !entries || !batch_id || count <= 0) return fail(BEGE_EINVAL, "bad argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaStream_t us = static_cast<cudaStream_t>(stream);
+  auto b = std::make_unique<Batch>();
+  b->cap = tail_capacity ? tail_capacity : ctx->cfg.tail_capacity;
+  size_t ny = 0, nD = 0, nAB = 0, nsig = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    const bege_batch_entry& en = entries[i];
+    if (!en.strain || en.reserved != 0 || en.reserved2 != 0.f)
+      return fail(BEGE_EINVAL, "batch entry: NULL strain or non-zero reserved field");
+    if (en.n != (1 << 14) && en.n != (1 << 15) && en.n != (1 << 16) && en.n != (1 << 17))
+      return fail(BEGE_EINVAL, "batch entry: n must be 2^14, 2^15, 2^16 or 2^17");
+    auto bi = ctx->banks.find(en.bank_id);
+    if (bi == ctx->banks.end()) return fail(BEGE_EINVAL, "batch entry: unknown bank handle");
+    if (bi->second->Lp > 4096)
+      return fail(BEGE_EINVAL, "batch entry: template longer than 4096 samples");
+    if (en.k_begin < 0 || en.k_end > bi->second->count || en.k_begin >= en.k_end)
+      return fail(BEGE_EINVAL, "batch entry: template range outside the bank or empty");
+    if (!std::isfinite(en.kappa) || en.kappa < 0.f)
+      return fail(BEGE_EINVAL, "batch entry: kappa must be finite and >= 0");
+    b->entries.push_back({en.n, en.bank_id, en.k_begin, en.k_end, en.kappa});
+    b->sigma_off.push_back(nsig);
+    ny += en.n;
+    nD += en.n / 2 + 1;
+    nAB += en.n / 2;
+    nsig += en.k_end - en.k_begin;
+  }
+  for (int64_t n : {1 << 14, 1 << 15, 1 << 16, 1 << 17}) {
+    std::shared_ptr<PlanHost> pl;
+    int rc = get_plan(ctx, n, &pl);
+    if (rc) return rc;
+    b->args.plans[log2i(n) - 14] = pl->dev;
+  }
+  struct Need {
+    DevBuf* d;
+    size_t bytes;
+  } need[] = {{&b->y, ny * 4}, {&b->D, nD * 8}, {&b->AB, nAB * 16},
+              {&b->segs, count * sizeof(bege::BatchSeg)}, {&b->queue, 16},
+              {&b->sigma, nsig * 4}, {&b->recs, (size_t)count * b->cap * sizeof(bege_tail)},
+              {&b->counters, (size_t)count * 8}};
+  for (auto& nd : need) {
+    int rc = ctx->alloc(nd.d, nd.bytes);
+    if (rc) {
+      destroy_batch(ctx, b.get());
+      return rc;
+    }
+  }
+  std::vector<bege::SegJob> jobs;
+  size_t oy = 0, oD = 0, oAB = 0;
+  cudaError_t e = cudaSuccess;
+  for (int32_t i = 0; i < count && e == cudaSuccess; ++i) {
+    const auto& en = b->entries[i];
+    Bank* bank = ctx->banks[en.bank].get();
+    float* y = static_cast<float*>(b->y.ptr) + oy;
+    float2* D = static_cast<float2*>(b->D.ptr) + oD;
+    float4* AB = static_cast<float4*>(b->AB.ptr) + oAB;
+    e = cudaMemcpyAsync(y, entries[i].strain, en.n * sizeof(float), cudaMemcpyHostToDevice, us);
+    const int S = (int)(en.n / 8192);
+    bege::BatchSeg sg{};
+    sg.AB = AB;
+    sg.bank = static_cast<const float*>(bank->w.ptr);
+    sg.Lp = bank->Lp;
+    sg.k0 = en.k0;
+    sg.k1 = en.k1;
+    sg.kappa = en.kappa;
+    sg.S = S;
+    sg.sigma = static_cast<float*>(b->sigma.ptr) + b->sigma_off[i];
+    sg.recs = static_cast<bege_tail*>(b->recs.ptr) + (size_t)i * b->cap;
+    sg.cap = b->cap;
+    sg.counter = static_cast<unsigned long long*>(b->counters.ptr) + i;
+    b->segs_host.push_back(sg);
+    for (int r = 0; r < S / 2; ++r) jobs.push_back({y, D, AB, S, r});
+    oy += en.n;
+    oD += en.n / 2 + 1;
+    oAB += en.n / 2;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->segs.ptr, b->segs_host.data(), count * sizeof(bege::BatchSeg),
+                        cudaMemcpyHostToDevice, us);
+  int rc = BEGE_OK;
+  if (e == cudaSuccess) rc = ctx->alloc(&b->jobs, jobs.size() * sizeof(bege::SegJob));
+  if (e == cudaSuccess && !rc)
+    e = cudaMemcpyAsync(b->jobs.ptr, jobs.data(), jobs.size() * sizeof(bege::SegJob),
+                        cudaMemcpyHostToDevice, us);
+  if (e == cudaSuccess && !rc) e = cudaStreamSynchronize(us);
+  if (e == cudaSuccess && !rc) e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !rc) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e == cudaSuccess && !rc) e = cudaEventCreate(&b->t0);
+  if (e == cudaSuccess && !rc) e = cudaEventCreate(&b->t1);
+  if (e != cudaSuccess || rc) {
+    destroy_batch(ctx, b.get());
+    return rc ? rc : cuda_fail(e, "batch setup");
+  }
+  b->n_jobs = (int)jobs.size();
+  b->args.segs = static_cast<const bege::BatchSeg*>(b->segs.ptr);
+  b->args.queue = static_cast<unsigned int*>(b->queue.ptr);
+  rc = batch_build(ctx, b.get());
+  if (rc) {
+    destroy_batch(ctx, b.get());
+    return rc;
+  }
+  const int32_t id = ctx->next_id++;
+  ctx->batches[id] = std::move(b);
+  *batch_id = id;
+  return BEGE_OK;
+}
+
+int bege_batch_run(bege_ctx* ctx, int32_t batch_id, void* stream) {
+  if (!ctx) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b = find_batch(ctx, batch_id);
+  if (!b) return fail(BEGE_EINVAL, "unknown batch handle");
+  return batch_run_locked(b, static_cast<cudaStream_t>(stream));
+}
+
+int bege_batch_elapsed_ms(bege_ctx* ctx, int32_t batch_id, float* ms) {
+  if (!ctx || !ms) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b = find_batch(ctx, batch_id);
+  if (!b) return fail(BEGE_EINVAL, "unknown batch handle");
+  int rc = batch_wait(b);
+  if (rc) return rc;
+  cudaError_t e = cudaEventElapsedTime(ms, b->t0, b->t1);
+  if (e != cudaSuccess) return cuda_fail(e, "batch time");
+  return BEGE_OK;
+}
+
+int bege_batch_fetch_tails(bege_ctx* ctx, int32_t batch_id, int32_t entry, bege_tail* out,
+                           int64_t capacity, int64_t* n_written, int64_t* n_total) {
+  if (!ctx || !n_written || !n_total) return fail(BEGE_EINVAL, "NULL argument");
+  if (capacity < 0 || (capacity > 0 && !out)) return fail(BEGE_EINVAL, "bad output buffer");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b = find_batch(ctx, batch_id);
+  if (!b) return fail(BEGE_EINVAL, "unknown batch handle");
+  if (entry < 0 || entry >= (int32_t)b->entries.size()) return fail(BEGE_EINVAL, "bad entry");
+  int rc = batch_wait(b);
+  if (rc) return rc;
+  unsigned long long total = 0;
+  cudaError_t e = cudaMemcpy(&total, static_cast<unsigned long long*>(b->counters.ptr) + entry,
+                             sizeof(total), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "tail count");
+  uint64_t ncopy = std::min<uint64_t>(std::min<uint64_t>(total, b->cap), (uint64_t)capacity);
+  if (ncopy) {
+    e = cudaMemcpy(out, static_cast<bege_tail*>(b->recs.ptr) + (size_t)entry * b->cap,
+                   ncopy * sizeof(bege_tail), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "tail records");
+  }
+  *n_written = (int64_t)ncopy;
+  *n_total = (int64_t)total;
+  if (ncopy < total) return fail(BEGE_EOVERFLOW, "more tails than copied");
+  return BEGE_OK;
+}
+
+int bege_batch_get_sigma(bege_ctx* ctx, int32_t batch_id, int32_t entry, float* out,
+                         int64_t count) {
+  if (!ctx || !out) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b = find_batch(ctx, batch_id);
+  if (!b) return fail(BEGE_EINVAL, "unknown batch handle");
+  if (entry < 0 || entry >= (int32_t)b->entries.size()) return fail(BEGE_EINVAL, "bad entry");
+  if (count != b->entries[entry].k1 - b->entries[entry].k0)
+    return fail(BEGE_EINVAL, "count must equal k_end - k_begin");
+  int rc = batch_wait(b);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpy(out, static_cast<float*>(b->sigma.ptr) + b->sigma_off[entry],
+                             (size_t)count * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "sigma");
+  return BEGE_OK;
+}
+
+int bege_batch_set_plan(bege_ctx* ctx, int32_t batch_id, int32_t plan, int64_t chunk,
+                        int32_t order) {
+  if (!ctx) return fail(BEGE_EINVAL, "NULL argument");
+  if (plan < 0 || plan > 1 || chunk < 1 || order < 0 || order > 1)
+    return fail(BEGE_EINVAL, "bad plan");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b = find_batch(ctx, batch_id);
+  if (!b) return fail(BEGE_EINVAL, "unknown batch handle");
+  if (b->done) cudaEventSynchronize(b->done);
+  b->plan = plan;
+  b->chunk = chunk;
+  b->order = order;
+  return batch_build(ctx, b);
+}
+
+int bege_batch_get_plan(bege_ctx* ctx, int32_t batch_id, int32_t* plan, int64_t* chunk,
+                        int32_t* order) {
+  if (!ctx || !plan || !chunk || !order) return fail(BEGE_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b = find_batch(ctx, batch_id);
+  if (!b) return fail(BEGE_EINVAL, "unknown batch handle");
+  *plan = b->plan;
+  *chunk = b->chunk;
+  *order = b->order;
+  return BEGE_OK;
+}
+
+int bege_batch_autotune(bege_ctx* ctx, int32_t batch_id, int32_t reps, void* stream,
+                        float* best_ms) {
+  if (!ctx || !best_ms || reps < 1) return fail(BEGE_EINVAL, "bad argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b = find_batch(ctx, batch_id);
+  if (!b) return fail(BEGE_EINVAL, "unknown batch handle");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  struct Cand {
+    int32_t plan;
+    int64_t chunk;
+    int32_t order;
+  };
+  std::vector<Cand> cands;
+  for (int64_t c : {64, 128, 256, 512, 1024, 2048})
+    for (int32_t o : {0, 1}) cands.push_back({0, c, o});
+  cands.push_back({1, b->chunk, 0});
+  float best = 0.f;
+  Cand pick = cands[0];
+  for (size_t i = 0; i < cands.size(); ++i) {
+    b->plan = cands[i].plan;
+    b->chunk = cands[i].chunk;
+    b->order = cands[i].order;
+    int rc = batch_build(ctx, b);
+    if (rc) return rc;
+    std::vector<float> t;
+    for (int r = 0; r <= reps; ++r) {
+      rc = batch_run_locked(b, s);
+      if (rc) return rc;
+      cudaError_t e = cudaEventSynchronize(b->done);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->t0, b->t1);
+      if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+      if (r > 0) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    const float med = t[t.size() / 2];
+    if (i == 0 || med < best) {
+      best = med;
+      pick = cands[i];
+    }
+  }
+  b->plan = pick.plan;
+  b->chunk = pick.chunk;
+  b->order = pick.order;
+  *best_ms = best;
+  return batch_build(ctx, b);
+}
+
 int bege_release(bege_ctx* ctx, int32_t handle) {
   if (!ctx) return fail(BEGE_EINVAL, "NULL argument");
   DeviceGuard dg(ctx->device);
@@ -765,6 +1205,12 @@ int bege_release(bege_ctx* ctx, int32_t handle) {
     destroy_job_events(ji->second.get());
     ctx->pool.push_back(std::move(ji->second->buf));
     ctx->jobs.erase(ji);
+    return BEGE_OK;
+  }
+  auto bti = ctx->batches.find(handle);
+  if (bti != ctx->batches.end()) {
+    destroy_batch(ctx, bti->second.get());
+    ctx->batches.erase(bti);
     return BEGE_OK;
   }
   auto si = ctx->segs.find(handle);

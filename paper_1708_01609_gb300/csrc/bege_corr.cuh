@@ -129,22 +129,29 @@ struct ColMap {
   }
 };
 
-// Load the per-N twiddle tables into shared memory and resolve the
-// (possibly remote) address of every column.
+// Twiddle tables that depend on F only (the Stockham passes).
+template <int F, int NC, int T>
+__device__ void setup_common(const PlanDev& p) {
+  using SM = Smem<F, NC>;
+  for (int i = threadIdx.x; i < F; i += T) SM::tw3()[i] = p.tw3[i];
+  for (int i = threadIdx.x; i < 16 * (F / 256); i += T) SM::tw2()[i] = p.tw2[i];
+}
+
+// Column twiddles of this CTA's slots (rank `grank` within its group of
+// C = S/NC CTAs) and the (possibly remote) address of every column of the
+// group, whose first CTA has cluster rank `gbase`.
 template <int F, int S, int NC, int T>
-__device__ void setup_tables(const PlanDev& p, int rank, bool map_columns) {
+__device__ void setup_columns(const PlanDev& p, int grank, int gbase, bool map_columns) {
   using SM = Smem<F, NC>;
   using CM = ColMap<S, NC>;
   const int t = threadIdx.x;
-  for (int i = t; i < F; i += T) SM::tw3()[i] = p.tw3[i];
-  for (int i = t; i < 16 * (F / 256); i += T) SM::tw2()[i] = p.tw2[i];
   for (int i = t; i < NC * 256; i += T) {
     const int c = i >> 8, j = i & 255;
-    SM::twin()[i] = p.wH[CM::slot_column(rank, c) * j];
+    SM::twin()[i] = p.wH[CM::slot_column(grank, c) * j];
   }
   for (int i = t; i < NC * 16; i += T) {
     const int c = i >> 4, r = i & 15;
-    const int b = CM::slot_column(rank, c);
+    const int b = CM::slot_column(grank, c);
     SM::rin()[i] = r < F / 256 ? p.wR0S[b * r] : make_float2(1.f, 0.f);
     SM::rout()[i] = cconj(p.w16S[b * r]);
   }
@@ -153,7 +160,7 @@ __device__ void setup_tables(const PlanDev& p, int rank, bool map_columns) {
     int owner, slot;
     CM::home(t, &owner, &slot);
     cg::cluster_group cl = cg::this_cluster();
-    float2* base = cl.map_shared_rank(SM::cols(), (unsigned)owner);
+    float2* base = cl.map_shared_rank(SM::cols(), (unsigned)(gbase + owner));
     SM::colptr()[t] = base + slot * col_stride<F>();
   }
 }
@@ -432,14 +439,14 @@ __device__ __forceinline__ float fused_mid(int rank, const float4* __restrict__ 
 // S1: segment spectrum D and product coefficients A, B (grid: C CTAs)
 // ---------------------------------------------------------------------------
 template <int F, int S, int NC, int T>
-__global__ void __launch_bounds__(T, 1)
-segment_kernel(PlanDev p, const float* __restrict__ y, float2* __restrict__ D,
-               float4* __restrict__ AB) {
+__device__ __forceinline__ void segment_body(const PlanDev& p, int rank,
+                                             const float* __restrict__ y,
+                                             float2* __restrict__ D, float4* __restrict__ AB) {
   using SM = Smem<F, NC>;
   constexpr int UPC = ColMap<S, NC>::UPC;
   const int H = p.g.H;
-  const int rank = blockIdx.x;
-  setup_tables<F, S, NC, T>(p, rank, false);
+  setup_common<F, NC, T>(p);
+  setup_columns<F, S, NC, T>(p, rank, 0, false);
   __syncthreads();
   forward_columns<F, S, NC, T, false>(rank, y, H, S);
 
@@ -488,12 +495,27 @@ segment_kernel(PlanDev p, const float* __restrict__ y, float2* __restrict__ D,
   }
 }
 
+template <int F, int S, int NC, int T>
+__global__ void __launch_bounds__(T, 1)
+segment_kernel(PlanDev p, const float* __restrict__ y, float2* __restrict__ D,
+               float4* __restrict__ AB) {
+  segment_body<F, S, NC, T>(p, blockIdx.x, y, D, AB);
+}
+
 // ---------------------------------------------------------------------------
 // S2-S6: template spectrum, product, sigma, inverse FFT, threshold, compaction
 // ---------------------------------------------------------------------------
+// Where one correlation's tails (and optional full dump) go.
+struct TailOut {
+  bege_tail* recs;
+  uint64_t cap;
+  unsigned long long* counter;
+  float* dump;
+};
+
 template <int F, int S, int NC, int T>
 __device__ __forceinline__ void combine_and_emit(int H, int rank, float thr, uint32_t tmpl,
-                                                 int64_t krow, const CorrelateArgs& a) {
+                                                 int64_t krow, const TailOut& a) {
   using SM = Smem<F, NC>;
   constexpr int C = ColMap<S, NC>::C;
   constexpr int per = F / C;
@@ -553,56 +575,45 @@ __device__ __forceinline__ void combine_and_emit(int H, int rank, float thr, uin
   }
 }
 
-template <int F, int S, int NC, int T, int MINB, bool HALFZ>
-__global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, CorrelateArgs a) {
+// S2-S5 for one template on this CTA's columns; leaves the CTA's share of
+// sum |Y|^2 in its sigpart slot and T_b in its columns (the caller
+// synchronises the cluster before the combine).
+template <int F, int S, int NC, int T, bool HALFZ>
+__device__ __forceinline__ void template_columns(int grank, const float* __restrict__ src, int nz,
+                                                 int nfold, const float4* __restrict__ AB) {
   using SM = Smem<F, NC>;
-  using CM = ColMap<S, NC>;
-  constexpr int C = CM::C;
-  constexpr int UPC = CM::UPC;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int N = p.g.N, H = p.g.H;
-  const int rank = (int)cluster.block_rank();
-  setup_tables<F, S, NC, T>(p, rank, true);
-  __syncthreads();
-
-  const int cid = blockIdx.x / C;
-  const int ncl = gridDim.x / C;
-  const int nz = (int)(a.Lp / 2);
-  const int nfold = (nz + F - 1) / F;
+  constexpr int UPC = ColMap<S, NC>::UPC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
-    if constexpr (F == 4096) {
-      // S2: forward passes 1-2; S2-S5 fused: forward pass 3, the product
-      // Y = conj(Z) A + Z' B with sum |Y|^2, inverse pass 1; S5: passes 2-3
-      fwd_first_pass<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold);
-      stockham_pass<F, NC, T, 16, 16, false>(SM::cols(), SM::tw2());
-      fused_mid<S, NC, T>(rank, a.AB, SM::red());
-      if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
-        *SM::sigpart() = s;
-      }
-      __syncthreads();
-      stockham_pass<F, NC, T, 16, 16, true>(SM::cols(), SM::tw2());
-      inv_last_pass<F, S, NC, T>();
-    } else {
+  if constexpr (F == 4096) {
+    // S2: forward passes 1-2; S2-S5 fused: forward pass 3, the product
+    // Y = conj(Z) A + Z' B with sum |Y|^2, inverse pass 1; S5: passes 2-3
+    fwd_first_pass<F, S, NC, T, HALFZ>(grank, src, nz, nfold);
+    stockham_pass<F, NC, T, 16, 16, false>(SM::cols(), SM::tw2());
+    fused_mid<S, NC, T>(grank, AB, SM::red());
+    if (threadIdx.x == 0) {
+      float s = 0.f;
+      for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
+      *SM::sigpart() = s;
+    }
+    __syncthreads();
+    stockham_pass<F, NC, T, 16, 16, true>(SM::cols(), SM::tw2());
+    inv_last_pass<F, S, NC, T>();
+  } else {
     // S2: template spectrum (column FFTs of the packed, twiddled template)
-    forward_columns<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold);
-
+    forward_columns<F, S, NC, T, HALFZ>(grank, src, nz, nfold);
     // S3 + S4: Y = conj(Z) A + Z' B over this CTA's bin pairs, sum |Y|^2
     float acc = 0.f;
 #pragma unroll
     for (int ui = 0; ui < UPC; ++ui) {
-      const int ug = rank * UPC + ui;
+      const int ug = grank * UPC + ui;
       const int count = unit_items<F, S>(ug);
 #pragma unroll 2
       for (int it = threadIdx.x; it < count; it += T) {
         const PairItem q = pair_item<F, S>(ug, ui, it);
         float2* cj = SM::col(q.sj) + pad(q.a);
         float2* cp = SM::col(q.sp) + pad(q.ap);
-        const float4 abj = __ldcg(a.AB + q.b * F + q.a);
-        const float4 abp = __ldcg(a.AB + q.bp * F + q.ap);
+        const float4 abj = __ldcg(AB + q.b * F + q.a);
+        const float4 abp = __ldcg(AB + q.bp * F + q.ap);
         const float2 zj = *cj, zp = *cp;
         const float2 yj = cadd(cconjmul(zj, make_float2(abj.x, abj.y)),
                                cmul(zp, make_float2(abj.z, abj.w)));
@@ -624,24 +635,49 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
       for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
       *SM::sigpart() = s;
     }
-
     // S5: inverse column FFTs (the first pass reads after the barrier above)
     inverse_columns<F, S, NC, T>();
-    }
+  }
+}
 
-    cluster.sync();  // every column and every sigma partial of the cluster is ready
-
-    float tot = 0.f;
+// sigma from the sum |Y|^2 partials of the C CTAs of a group (Eq. PT on the
+// packed spectrum: sigma^2 = 2 sum |Y|^2 / N^2).
+template <int F, int S, int NC>
+__device__ __forceinline__ float group_sigma(int gbase, int N) {
+  using SM = Smem<F, NC>;
+  constexpr int C = ColMap<S, NC>::C;
+  cg::cluster_group cluster = cg::this_cluster();
+  float tot = 0.f;
 #pragma unroll
-    for (int q = 0; q < C; ++q) tot += *cluster.map_shared_rank(SM::sigpart(), (unsigned)q);
-    const float sigma = sqrtf(2.0f * tot) / (float)N;
-    const float thr = a.kappa * sigma;
+  for (int q = 0; q < C; ++q)
+    tot += *cluster.map_shared_rank(SM::sigpart(), (unsigned)(gbase + q));
+  return sqrtf(2.0f * tot) / (float)N;
+}
+
+template <int F, int S, int NC, int T, int MINB, bool HALFZ>
+__global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, CorrelateArgs a) {
+  constexpr int C = ColMap<S, NC>::C;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int N = p.g.N, H = p.g.H;
+  const int rank = (int)cluster.block_rank();
+  setup_common<F, NC, T>(p);
+  setup_columns<F, S, NC, T>(p, rank, 0, true);
+  __syncthreads();
+
+  const int cid = blockIdx.x / C;
+  const int ncl = gridDim.x / C;
+  const int nz = (int)(a.Lp / 2);
+  const int nfold = (nz + F - 1) / F;
+  const TailOut out{a.recs, a.cap, a.counter, a.dump};
+
+  for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
+    template_columns<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold, a.AB);
+    cluster.sync();  // every column and every sigma partial of the cluster is ready
+    const float sigma = group_sigma<F, S, NC>(0, N);
     const int64_t krow = k - a.k0;
     if (rank == 0 && threadIdx.x == 0) a.sigma[krow] = sigma;
-
     // S6: S-point combine, threshold, warp-ballot compaction
-    combine_and_emit<F, S, NC, T>(H, rank, thr, (uint32_t)k, krow, a);
-
+    combine_and_emit<F, S, NC, T>(H, rank, a.kappa * sigma, (uint32_t)k, krow, out);
     cluster.sync();  // remote reads done before the columns are overwritten
   }
 }

@@ -182,3 +182,39 @@ def random_samples_bank(count: int, length: int, seed: int) -> np.ndarray:
     feed identical template samples to both sides."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal((count, length)).astype(np.float32)
+
+
+@dataclasses.dataclass
+class BatchEntry:
+    seg: Segment
+    tau: float
+    k0: int          # sub-bank: rows [k0, k1) of the bank for this tau
+    k1: int
+
+
+def batch_case(seed: int = 4242, n_segments: int = 64, n_inject: int = 8,
+               sizes=(1 << 14, 1 << 15, 1 << 16, 1 << 17),
+               sub_bank=(1 << 12, 1 << 16), taus=(0.5, 1.0), n_fdot: int = 1024,
+               n_f0: int = 1024):
+    """Batching-form workload: segments of lengths drawn uniformly from
+    ``sizes``, each with its own sub-bank (a contiguous row range of the
+    in-band grid for its tau, size log-uniform in ``sub_bank``) and
+    ``n_inject`` injections drawn from that sub-bank.
+
+    Returns (entries, {tau: params}).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    grids = {tau: grid_paper(n_fdot, n_f0, tau=tau) for tau in taus}
+    entries = []
+    for s in range(n_segments):
+        n = int(rng.choice(sizes))
+        tau = float(rng.choice(taus))
+        size = int(round(2.0 ** rng.uniform(math.log2(sub_bank[0]), math.log2(sub_bank[1]))))
+        total = len(grids[tau])
+        size = min(size, total)
+        k0 = int(rng.integers(0, total - size + 1))
+        sub = grids[tau][k0:k0 + size]
+        seg = make_segment(n, sub, n_inject, seed * 1000 + s, tau=tau)
+        seg.injections = [(k + k0, lag, a) for k, lag, a in seg.injections]
+        entries.append(BatchEntry(seg=seg, tau=tau, k0=k0, k1=k0 + size))
+    return entries, grids
