@@ -233,6 +233,44 @@ int bege_batch_get_plan(bege_ctx* ctx, int32_t batch_id, int32_t* plan, int64_t*
 int bege_batch_autotune(bege_ctx* ctx, int32_t batch_id, int32_t reps, void* stream,
                         float* best_ms);
 
+/* ---- Search without device allocation -----------------------------------
+ * The paper has no counterpart of this call.  It serves callers that may not
+ * allocate device memory themselves or have a library do it for them: for
+ * example a program whose device memory all belongs to one pool it manages
+ * (a framework's caching allocator, or an arena reserved at start-up so that
+ * a latency-critical loop never calls cudaMalloc/cudaFree).  It runs the
+ * whole search of one segment -- spectrum, correlation with bank rows
+ * [k_begin, k_end), sigma and tails -- using only the caller's buffers plus
+ * one fixed scratch array inside the library (about 1.05 MiB of device
+ * memory per GPU, held from library load until process exit).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   strain_dev      DEVICE, n FP32 samples, 8-byte aligned
+ *   n               power of two in [2^10, 2^16] (the scratch holds at most
+ *                   2^16 samples; larger n is rejected with BEGE_EINVAL)
+ *   bank_dev        DEVICE, rows of `ld` FP32 samples, 32-byte aligned; row k
+ *                   holds template k, zero beyond its length
+ *   ld              row stride in floats, a multiple of 8, at most n
+ *   kappa           finite, >= 0
+ *   sigma_dev       DEVICE, k_end - k_begin FP32: sigma of row k at k - k_begin
+ *   tails_dev       DEVICE, tail_capacity records (bege_tail)
+ *   tail_count_dev  DEVICE, one unsigned 64-bit count, 8-byte aligned; set to
+ *                   zero by the call, then to the true number of tails (only
+ *                   the first tail_capacity records are stored)
+ *   stream          cudaStream_t as void*; the call only enqueues work
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current) and every call with a new n recomputes the
+ * twiddle tables in the scratch array, so the first call on each device
+ * should come before any stream capture.  The scratch array keeps the last
+ * call's contents and is shared by all calls on a device: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller.  Errors:
+ * EINVAL (sizes, alignment, NULL), ECUDA. */
+int bege_search_noalloc(const float* strain_dev, int64_t n, const float* bank_dev, int64_t ld,
+                        int64_t k_begin, int64_t k_end, float kappa, float* sigma_dev,
+                        bege_tail* tails_dev, uint64_t tail_capacity,
+                        unsigned long long* tail_count_dev, void* stream);
+
 /* Release a segment, bank, job or batch handle and its device memory (job
  * buffers return to the context's pool).  Errors: EINVAL for an unknown
  * handle. */

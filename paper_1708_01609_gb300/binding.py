@@ -95,6 +95,8 @@ SIGNATURES = {
     "bege_batch_set_plan": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I32]),
     "bege_batch_get_plan": (ctypes.c_int, [_VP, _I32, _PI32, _PI64, _PI32]),
     "bege_batch_autotune": (ctypes.c_int, [_VP, _I32, _I32, _VP, ctypes.POINTER(ctypes.c_float)]),
+    "bege_search_noalloc": (ctypes.c_int, [_VP, _I64, _VP, _I64, _I64, _I64, ctypes.c_float, _VP,
+                                           _VP, ctypes.c_uint64, _VP, _VP]),
     "bege_release": (ctypes.c_int, [_VP, _I32]),
     "bege_last_error": (ctypes.c_char_p, [_VP]),
     "bege_version": (ctypes.c_char_p, []),
@@ -343,6 +345,17 @@ class Context:
 
     def bege_device_bytes(self) -> int:
         return int(self.lib.bege_device_bytes(self.h))
+
+
+def bege_search_noalloc(strain_dev: int, n: int, bank_dev: int, ld: int, k_begin: int,
+                        k_end: int, kappa: float, sigma_dev: int, tails_dev: int,
+                        tail_capacity: int, tail_count_dev: int, stream: int = 0) -> None:
+    """Search of one segment that allocates no device memory: every pointer is
+    a device address owned by the caller (see include/bege.h)."""
+    lib = load_library()
+    _check(lib.bege_search_noalloc(strain_dev, n, bank_dev, ld, k_begin, k_end, kappa,
+                                   sigma_dev, tails_dev, tail_capacity, tail_count_dev, stream),
+           "bege_search_noalloc")
 
 
 def bege_version() -> str:

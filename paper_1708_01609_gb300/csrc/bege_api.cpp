@@ -52,6 +52,10 @@ struct DevBuf {
 
 }  // namespace
 
+namespace bege {
+int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace bege
+
 struct PlanHost {
   bege::Geometry g{};
   bege::PlanDev dev{};

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/bege.h"
 
 namespace bege {
@@ -50,6 +52,10 @@ struct PlanDev {
 };
 
 Geometry make_geometry(int64_t n);
+
+// Record `msg` as the calling thread's last error (bege_last_error) and
+// return `code`.
+int set_last_error(int code, const std::string& msg);
 
 // Launch shapes compiled for geometry g (at most `max`); returns the count.
 int correlate_configs(const Geometry& g, CorrConfig* out, int max);
