@@ -374,14 +374,99 @@ def run_batch_form(args):
     return 0
 
 
+def run_serve_form(args):
+    """Serving form: two channels of band-limited noise emit 8, 16 and 32 s
+    segments with Poisson arrivals at 2x real time; every request searches the
+    resident 2^20-chirp bank at kappa 5.5 under a 120 GB device budget.
+    Paced run: latency (p50/p99), throughput, real-time factor.  Saturated
+    run (every request submitted at once): capacity."""
+    import threading
+
+    import torch
+    from paper_1708_01609_gb300 import binding, build
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    build()
+    budget = 120 * 10**9
+    ctx = binding.Context(0, tail_capacity=1 << 21, hbm_budget_bytes=budget)
+    params = S.grid_paper()
+    bank = ctx.bege_define_bank(params, tau=1.0, taper_frac=0.05)
+    count = len(params)
+    sv = ctx.bege_serve_create(bank, KAPPA, streams=args.serve_streams,
+                               slice_templates=args.serve_slice,
+                               hbm_budget_bytes=budget - ctx.bege_device_bytes())
+    warm = S.serving_stream(3, seed=1)
+    for a in warm:
+        ctx.bege_serve_wait(sv, ctx.bege_serve_submit(sv, a.y, a.channel))
+
+    def run(arrivals, paced):
+        ids = [None] * len(arrivals)
+        t0 = time.monotonic()
+
+        def feed():
+            for i, a in enumerate(arrivals):
+                if paced:
+                    delay = t0 + a.t - time.monotonic()
+                    if delay > 0:
+                        time.sleep(delay)
+                ids[i] = ctx.bege_serve_submit(sv, a.y, a.channel)
+
+        th = threading.Thread(target=feed)
+        th.start()
+        th.join()
+        infos = []
+        for rid in ids:
+            ctx.bege_serve_wait(sv, rid)
+            infos.append(ctx.bege_serve_info_get(sv, rid))
+            ctx.bege_serve_forget(sv, rid)
+        lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
+        span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+        data_s = sum(a.n for a in arrivals) / S.FS
+        return {
+            "requests": len(arrivals), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "mean_ms": float(lat.mean()), "wall_s": span,
+            "correlations_per_s": len(arrivals) * count / span,
+            "real_time_factor": data_s / span / 2.0,
+            "tails_per_request_mean": float(np.mean([i["n_tails"] for i in infos])),
+            "tails_per_request_max": int(max(i["n_tails"] for i in infos)),
+            "segment_lengths": sorted({a.n for a in arrivals}),
+        }
+
+    paced = run(S.serving_stream(args.serve_requests, seed=2024, speed=2.0), paced=True)
+    burst = run(S.serving_stream(args.serve_burst, seed=7, speed=2.0), paced=False)
+    ctx.bege_serve_destroy(sv)
+    line = {
+        "form": "serve", "metric": "served p99 latency, 2x real time, 2^20-chirp bank",
+        "value": paced["p99_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": ("two channels of band-limited noise, 8/16/32 s segments, "
+                                "Poisson arrivals at 2x real time per channel, full 2^20 "
+                                "chirp bank per request, kappa 5.5, 120 GB device budget"),
+                   "streams": args.serve_streams, "slice_templates": args.serve_slice},
+        "paced": paced,
+        "saturated": burst,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["search", "batch"], default="search",
-                    help="search: the headline N=2^16 x 2^20 step; batch: the batching form")
+    ap.add_argument("--form", choices=["search", "batch", "serve"], default="search",
+                    help="search: the headline N=2^16 x 2^20 step; batch: the batching form; "
+                         "serve: the serving form")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the paced serving run (arrivals at 2x real time)")
+    ap.add_argument("--serve-burst", type=int, default=24,
+                    help="requests of the saturated serving run")
+    ap.add_argument("--serve-streams", type=int, default=3)
+    ap.add_argument("--serve-slice", type=int, default=65536)
     ap.add_argument("--templates", type=int, default=1 << 20,
                     help="bank rows per step (the benchmark uses all 2^20)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -393,6 +478,8 @@ def main():
         return run_reference(args)
     if args.form == "batch":
         return run_batch_form(args)
+    if args.form == "serve":
+        return run_serve_form(args)
     return run_ours(args)
 
 

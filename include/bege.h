@@ -233,6 +233,73 @@ int bege_batch_get_plan(bege_ctx* ctx, int32_t batch_id, int32_t* plan, int64_t*
 int bege_batch_autotune(bege_ctx* ctx, int32_t batch_id, int32_t reps, void* stream,
                         float* best_ms);
 
+/* ---- Serving form ----------------------------------------------------------
+ * A request loop with continuous batching over one resident bank (the paper's
+ * low-latency use, Sec. 1, Sec. 6).  Requests are strain segments submitted
+ * from any number of detector channels as they arrive.  A server thread
+ * admits them in arrival order while the device bytes its requests hold stay
+ * within the budget, loads each admitted segment's spectrum, cuts its
+ * correlation with the whole bank into slices of `slice_templates` rows and
+ * keeps up to `streams` slices in flight on separate CUDA streams, taking
+ * slices round-robin from every admitted request: a request that arrives
+ * while others run starts within one slice and its work overlaps theirs on
+ * the device.  Every template sees the same kernel arithmetic whatever else
+ * runs, so results do not depend on the mix.  When a request's last slice
+ * completes its tails and sigma are copied to host memory and its device
+ * memory is released.  bege_destroy stops the context's servers first. */
+typedef struct {
+  int32_t bank_id;
+  int32_t streams;            /* slices in flight at once; 0 = 3                  */
+  int64_t slice_templates;    /* bank rows per slice; 0 = 65536                   */
+  float kappa;                /* threshold for every request (finite, >= 0)       */
+  float reserved;             /* must be 0                                        */
+  uint64_t hbm_budget_bytes;  /* device bytes the admitted requests may hold
+                                 (segment spectra and slice buffers); 0 = only the
+                                 context's own budget applies                     */
+} bege_serve_config;
+
+typedef struct {
+  int32_t state;      /* 0 queued, 1 admitted (running), 2 done, 3 failed       */
+  int32_t channel;    /* as submitted                                           */
+  int64_t n;          /* segment length                                         */
+  int64_t n_tails;    /* tail count (valid when done)                           */
+  double t_submit;    /* host monotonic clock, seconds: submitted               */
+  double t_admit;     /*   admitted                                             */
+  double t_done;      /*   results on the host                                  */
+  double gpu_ms;      /* summed kernel time of the request's slices             */
+} bege_serve_info;
+
+/* Start a server thread on `cfg->bank_id`.  *server_id receives the handle. */
+int bege_serve_create(bege_ctx* ctx, const bege_serve_config* cfg, int32_t* server_id);
+
+/* Queue a request: `strain` is a HOST array of n FP32 samples (copied before
+ * the call returns; n a power of two in [2^10, 2^17], at least the bank's
+ * template length).  *request_id receives a per-server id. */
+int bege_serve_submit(bege_ctx* ctx, int32_t server_id, const float* strain, int64_t n,
+                      int32_t channel, int64_t* request_id);
+
+/* Block until the request is done (BEGE_OK), failed (its error), or
+ * `timeout_ms` passes (BEGE_ETIMEDOUT; < 0 waits without limit). */
+int bege_serve_wait(bege_ctx* ctx, int32_t server_id, int64_t request_id, int32_t timeout_ms);
+
+/* State and timings of a request. */
+int bege_serve_info_get(bege_ctx* ctx, int32_t server_id, int64_t request_id,
+                        bege_serve_info* info);
+
+/* Results of a done request, from host memory: tails (same conventions as
+ * bege_fetch_tails) and sigma of every bank row (`count` = bank size). */
+int bege_serve_fetch_tails(bege_ctx* ctx, int32_t server_id, int64_t request_id, bege_tail* out,
+                           int64_t capacity, int64_t* n_written, int64_t* n_total);
+int bege_serve_get_sigma(bege_ctx* ctx, int32_t server_id, int64_t request_id, float* out,
+                         int64_t count);
+
+/* Drop a done request's host-side results. */
+int bege_serve_forget(bege_ctx* ctx, int32_t server_id, int64_t request_id);
+
+/* Stop the server after the work in flight completes; queued requests that
+ * were not admitted are dropped. */
+int bege_serve_destroy(bege_ctx* ctx, int32_t server_id);
+
 /* ---- Search without device allocation -----------------------------------
  * The paper has no counterpart of this call.  It serves callers that may not
  * allocate device memory themselves or have a library do it for them: for

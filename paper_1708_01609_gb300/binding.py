@@ -51,6 +51,19 @@ class bege_batch_entry(ctypes.Structure):
                 ("kappa", ctypes.c_float), ("reserved2", ctypes.c_float)]
 
 
+class bege_serve_config(ctypes.Structure):
+    _fields_ = [("bank_id", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("slice_templates", ctypes.c_int64), ("kappa", ctypes.c_float),
+                ("reserved", ctypes.c_float), ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class bege_serve_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("channel", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("n_tails", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("gpu_ms", ctypes.c_double)]
+
+
 class bege_tail(ctypes.Structure):
     _fields_ = [("tmpl", ctypes.c_uint32), ("lag", ctypes.c_uint32), ("value", ctypes.c_float)]
 
@@ -97,6 +110,14 @@ SIGNATURES = {
     "bege_batch_autotune": (ctypes.c_int, [_VP, _I32, _I32, _VP, ctypes.POINTER(ctypes.c_float)]),
     "bege_search_noalloc": (ctypes.c_int, [_VP, _I64, _VP, _I64, _I64, _I64, ctypes.c_float, _VP,
                                            _VP, ctypes.c_uint64, _VP, _VP]),
+    "bege_serve_create": (ctypes.c_int, [_VP, ctypes.POINTER(bege_serve_config), _PI32]),
+    "bege_serve_submit": (ctypes.c_int, [_VP, _I32, _VP, _I64, _I32, _PI64]),
+    "bege_serve_wait": (ctypes.c_int, [_VP, _I32, _I64, _I32]),
+    "bege_serve_info_get": (ctypes.c_int, [_VP, _I32, _I64, ctypes.POINTER(bege_serve_info)]),
+    "bege_serve_fetch_tails": (ctypes.c_int, [_VP, _I32, _I64, _VP, _I64, _PI64, _PI64]),
+    "bege_serve_get_sigma": (ctypes.c_int, [_VP, _I32, _I64, _VP, _I64]),
+    "bege_serve_forget": (ctypes.c_int, [_VP, _I32, _I64]),
+    "bege_serve_destroy": (ctypes.c_int, [_VP, _I32]),
     "bege_release": (ctypes.c_int, [_VP, _I32]),
     "bege_last_error": (ctypes.c_char_p, [_VP]),
     "bege_version": (ctypes.c_char_p, []),
@@ -339,6 +360,56 @@ class Context:
         _check(self.lib.bege_batch_autotune(self.h, batch, reps, stream, ctypes.byref(ms)),
                "bege_batch_autotune")
         return float(ms.value)
+
+    # -- serving form ------------------------------------------------------
+    def bege_serve_create(self, bank: int, kappa: float, streams: int = 0,
+                          slice_templates: int = 0, hbm_budget_bytes: int = 0) -> int:
+        cfg = bege_serve_config(bank, streams, slice_templates, kappa, 0.0, hbm_budget_bytes)
+        sid = _I32()
+        _check(self.lib.bege_serve_create(self.h, ctypes.byref(cfg), ctypes.byref(sid)),
+               "bege_serve_create")
+        return sid.value
+
+    def bege_serve_submit(self, server: int, strain: np.ndarray, channel: int = 0) -> int:
+        y = np.ascontiguousarray(strain, dtype=np.float32)
+        rid = _I64()
+        _check(self.lib.bege_serve_submit(self.h, server, _ptr(y), len(y), channel,
+                                          ctypes.byref(rid)), "bege_serve_submit")
+        return rid.value
+
+    def bege_serve_wait(self, server: int, request: int, timeout_ms: int = -1) -> bool:
+        rc = _check(self.lib.bege_serve_wait(self.h, server, request, timeout_ms),
+                    "bege_serve_wait", ok=(BEGE_OK, BEGE_ETIMEDOUT))
+        return rc == BEGE_OK
+
+    def bege_serve_info_get(self, server: int, request: int) -> dict:
+        info = bege_serve_info()
+        _check(self.lib.bege_serve_info_get(self.h, server, request, ctypes.byref(info)),
+               "bege_serve_info_get")
+        return {f: getattr(info, f) for f, _ in bege_serve_info._fields_}
+
+    def bege_serve_fetch_tails(self, server: int, request: int):
+        nw, nt = _I64(), _I64()
+        _check(self.lib.bege_serve_fetch_tails(self.h, server, request, None, 0, ctypes.byref(nw),
+                                               ctypes.byref(nt)), "bege_serve_fetch_tails",
+               ok=(BEGE_OK, BEGE_EOVERFLOW))
+        out = np.empty(nt.value, dtype=TAIL_DTYPE)
+        _check(self.lib.bege_serve_fetch_tails(self.h, server, request, _ptr(out), len(out),
+                                               ctypes.byref(nw), ctypes.byref(nt)),
+               "bege_serve_fetch_tails", ok=(BEGE_OK, BEGE_EOVERFLOW))
+        return out[: nw.value], nt.value
+
+    def bege_serve_get_sigma(self, server: int, request: int, count: int) -> np.ndarray:
+        out = np.empty(count, dtype=np.float32)
+        _check(self.lib.bege_serve_get_sigma(self.h, server, request, _ptr(out), count),
+               "bege_serve_get_sigma")
+        return out
+
+    def bege_serve_forget(self, server: int, request: int) -> None:
+        _check(self.lib.bege_serve_forget(self.h, server, request), "bege_serve_forget")
+
+    def bege_serve_destroy(self, server: int) -> None:
+        _check(self.lib.bege_serve_destroy(self.h, server), "bege_serve_destroy")
 
     def bege_release(self, handle: int) -> None:
         _check(self.lib.bege_release(self.h, handle), "bege_release")

@@ -505,6 +505,7 @@ int bege_create(bege_ctx** out, int device, const bege_config* cfg) {
 
 int bege_destroy(bege_ctx* ctx) {
   if (!ctx) return fail(BEGE_EINVAL, "ctx is NULL");
+  bege::serve_destroy_all(ctx);
   {
     DeviceGuard dg(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -935,6 +936,19 @@ int64_t bege_segment_length(bege_ctx* ctx, int32_t seg_id) {
   auto si = ctx->segs.find(seg_id);
   return si == ctx->segs.end() ? 0 : si->second->n;
 }
+
+}  // extern "C"
+
+namespace bege {
+int ctx_device(const bege_ctx* ctx) { return ctx->device; }
+int64_t bank_count(bege_ctx* ctx, int32_t bank_id) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto bi = ctx->banks.find(bank_id);
+  return bi == ctx->banks.end() ? 0 : bi->second->count;
+}
+}  // namespace bege
+
+extern "C" {
 
 int64_t bege_bank_length(bege_ctx* ctx, int32_t bank_id) {
   if (!ctx) return 0;

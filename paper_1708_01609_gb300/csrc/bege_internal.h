@@ -57,6 +57,14 @@ Geometry make_geometry(int64_t n);
 // return `code`.
 int set_last_error(int code, const std::string& msg);
 
+// CUDA device of a context, and the row count of one of its banks (0 if the
+// handle is unknown).
+int ctx_device(const bege_ctx* ctx);
+int64_t bank_count(bege_ctx* ctx, int32_t bank_id);
+
+// Stop every serving-form server of a context.
+void serve_destroy_all(bege_ctx* ctx);
+
 // Launch shapes compiled for geometry g (at most `max`); returns the count.
 int correlate_configs(const Geometry& g, CorrConfig* out, int max);
 CorrConfig default_config(const Geometry& g);

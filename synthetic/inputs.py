@@ -218,3 +218,40 @@ def batch_case(seed: int = 4242, n_segments: int = 64, n_inject: int = 8,
         seg.injections = [(k + k0, lag, a) for k, lag, a in seg.injections]
         entries.append(BatchEntry(seg=seg, tau=tau, k0=k0, k1=k0 + size))
     return entries, grids
+
+
+@dataclasses.dataclass
+class Arrival:
+    t: float          # arrival time, seconds from the start of the stream
+    channel: int
+    n: int            # samples
+    y: np.ndarray     # FP32 strain
+
+
+def serving_stream(n_requests: int, seed: int = 99, channels: int = 2,
+                   durations=(8.0, 16.0, 32.0), speed: float = 2.0, fs: float = FS,
+                   n_inject: int = 0, params=None):
+    """Requests of the serving form: each channel emits band-limited noise
+    segments of durations drawn uniformly from ``durations`` with Poisson
+    arrivals whose mean rate carries ``speed`` data-seconds per wall-second
+    per channel (speed = 2: twice real time).  Returns the first
+    ``n_requests`` arrivals over all channels in time order.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rate = speed / float(np.mean(durations))  # requests per second per channel
+    per = []
+    for c in range(channels):
+        t = 0.0
+        for i in range(n_requests):
+            t += float(rng.exponential(1.0 / rate))
+            dur = float(rng.choice(durations))
+            per.append((t, c, int(round(dur * fs)), seed * 100000 + c * 10000 + i))
+    per.sort()
+    out = []
+    for t, c, n, s in per[:n_requests]:
+        if n_inject and params is not None:
+            y = make_segment(n, params, n_inject, s).y
+        else:
+            y = band_limited_noise(n, s, fs)
+        out.append(Arrival(t=t, channel=c, n=n, y=y))
+    return out
