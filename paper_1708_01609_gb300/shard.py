@@ -1,0 +1,90 @@
+"""Multi-rank host logic: bank shards, tail gathering, failed-rank re-queue.
+
+Every (segment, template) correlation is independent (the paper's partition
+of the bank into groups W_alpha and the data into blocks Y_beta, Sec. 3.1),
+so N ranks split a bank into contiguous row ranges, search their own range
+with no collective on the data path, and rank 0 concatenates the tails.  If
+a rank fails, the ranges it had not finished are re-queued to the ranks that
+are still alive.  The compute step is a callable, so the same logic drives
+GPU ranks (libbege) and CPU ranks in tests.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def shard_ranges(count: int, world: int) -> list[tuple[int, int]]:
+    """Contiguous [begin, end) row ranges, sizes differing by at most one."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    base, extra = divmod(count, world)
+    out, k = [], 0
+    for r in range(world):
+        n = base + (1 if r < extra else 0)
+        out.append((k, k + n))
+        k += n
+    return out
+
+
+def merge_tails(parts: list[np.ndarray]) -> np.ndarray:
+    """Concatenate per-rank tail records and order them by (tmpl, lag)."""
+    parts = [p for p in parts if p is not None and len(p)]
+    if not parts:
+        return np.empty(0, dtype=[("tmpl", np.uint32), ("lag", np.uint32), ("value", np.float32)])
+    t = np.concatenate(parts)
+    return np.sort(t, order=["tmpl", "lag"])
+
+
+def run_sharded(dist, compute, count: int, chunk: int, fail_rank: int | None = None,
+                fail_after: int = 0):
+    """Search rows [0, count) over all ranks of ``dist`` (an initialised
+    torch.distributed module) in chunks of ``chunk`` rows.
+
+    ``compute(k0, k1)`` returns this rank's tail records for rows [k0, k1).
+    Chunks are dealt round-robin; after every round the ranks exchange (on
+    the host, via all_gather_object) which chunks they finished.  A rank
+    that raises is treated as failed: it reports no more progress, and its
+    unfinished chunks are dealt again to the survivors.  ``fail_rank`` /
+    ``fail_after`` make that rank fail after that many chunks (fault
+    injection for tests).  Returns the merged tails on rank 0 (None
+    elsewhere) and the set of ranks that failed.
+    """
+    rank, world = dist.get_rank(), dist.get_world_size()
+    pending = [(k, min(k + chunk, count)) for k in range(0, count, chunk)]
+    alive = list(range(world))
+    failed: set[int] = set()
+    mine: list[np.ndarray] = []
+    done_here = 0
+    dead = False
+    while pending:
+        # deal the pending chunks round-robin over the live ranks
+        assign = {r: [] for r in alive}
+        for i, c in enumerate(pending):
+            assign[alive[i % len(alive)]].append(c)
+        finished, crashed = [], False
+        if not dead and rank in assign:
+            for c in assign[rank]:
+                try:
+                    if fail_rank == rank and done_here >= fail_after:
+                        raise RuntimeError(f"rank {rank} failed (injected)")
+                    mine.append(compute(*c))
+                    finished.append(c)
+                    done_here += 1
+                except RuntimeError:
+                    crashed = dead = True
+                    break
+        reports = [None] * world
+        dist.all_gather_object(reports, {"finished": finished, "crashed": crashed})
+        for r, rep in enumerate(reports):
+            if rep["crashed"]:
+                failed.add(r)
+        done = {c for rep in reports for c in rep["finished"]}
+        pending = [c for c in pending if c not in done]
+        alive = [r for r in alive if r not in failed]
+        if not alive:
+            raise RuntimeError("every rank failed")
+    gathered = [None] * world
+    dist.all_gather_object(gathered, merge_tails(mine))
+    if rank == 0:
+        return merge_tails(gathered), failed
+    return None, failed
