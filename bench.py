@@ -42,6 +42,7 @@ N_SAMPLES = 1 << 16
 KAPPA = 5.5
 METRIC = "chirp correlations/s at N=2^16"
 UNIT = "correlations/s"
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "fp16x2": 2}
 
 
 def workload_config(templates: int, world: int) -> dict:
@@ -216,7 +217,8 @@ def run_ours(args):
     from paper_1708_01609_gb300 import binding, build
     build()
     cap = 1 << 25   # all hits of 32 strong injections per segment run to ~1.4e7 records
-    ctx = binding.Context(local, tail_capacity=cap)
+    prec = PRECISIONS[args.precision]
+    ctx = binding.Context(local, tail_capacity=cap, precision=prec)
     templates = args.templates
     seg_data, params = S.paper_case(seed=2017 + rank)
     params = params[:templates]
@@ -469,6 +471,9 @@ def main():
     ap.add_argument("--serve-slice", type=int, default=65536)
     ap.add_argument("--templates", type=int, default=1 << 20,
                     help="bank rows per step (the benchmark uses all 2^20)")
+    ap.add_argument("--precision", choices=list(PRECISIONS), default="fp32",
+                    help="fp32: the plain path; bf16x3 / fp16x2: the precision form "
+                         "(column FFTs as split-operand tensor-core GEMMs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-templates", type=int, default=8,

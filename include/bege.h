@@ -51,7 +51,10 @@ typedef struct {
   double fs;                  /* sample rate in Hz (the paper: 4096, Sec. 3)     */
   uint64_t hbm_budget_bytes;  /* cap on library-owned device memory; 0 = none    */
   uint64_t tail_capacity;     /* device tail records per job; 0 = 1<<20          */
-  int32_t precision;          /* 0 = FP32 (the only value accepted for now)      */
+  int32_t precision;          /* 0 = FP32; 1 = BF16x3, 2 = FP16x2: the precision
+                                 form, column FFTs on tensor cores with split
+                                 (hi + lo) 16-bit operands, FP32 accumulation
+                                 (needs N >= 2^14, templates <= 4096 samples) */
   int32_t reserved;           /* must be 0                                       */
 } bege_config;
 
@@ -119,7 +122,8 @@ int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_beg
  * records).  *n_total receives the true number of tails; *n_written the
  * number copied = min(n_total, capacity, device tail capacity).  Records are
  * in device completion order (not sorted).  Returns BEGE_EOVERFLOW (with the
- * counts filled in) when n_total exceeds what was copied. */
+ * counts filled in) when n_total exceeds what was copied, BEGE_ETIMEDOUT if
+ * a bounded wait inside the kernel gave up (the job's results are invalid). */
 int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capacity,
                      int64_t* n_written, int64_t* n_total);
 

@@ -163,9 +163,9 @@ class Context:
     """One libbege context on one CUDA device (method names follow bege.h)."""
 
     def __init__(self, device: int = 0, fs: float = 4096.0, hbm_budget_bytes: int = 0,
-                 tail_capacity: int = 1 << 20):
+                 tail_capacity: int = 1 << 20, precision: int = 0):
         self.lib = load_library()
-        cfg = bege_config(fs, hbm_budget_bytes, tail_capacity, 0, 0)
+        cfg = bege_config(fs, hbm_budget_bytes, tail_capacity, precision, 0)
         h = _VP()
         _check(self.lib.bege_create(ctypes.byref(h), device, ctypes.byref(cfg)), "bege_create")
         self.h = h

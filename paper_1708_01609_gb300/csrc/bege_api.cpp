@@ -288,7 +288,7 @@ int take_job_buffers(bege_ctx* ctx, int64_t nsig, uint64_t cap, std::unique_ptr<
     ctx->release(&b->sigma);
     return rc;
   }
-  rc = ctx->alloc(&b->counter, sizeof(unsigned long long));
+  rc = ctx->alloc(&b->counter, 16);  // u64 tail count, u32 status
   if (rc) {
     ctx->release(&b->sigma);
     ctx->release(&b->recs);
@@ -484,7 +484,8 @@ int bege_create(bege_ctx** out, int device, const bege_config* cfg) {
     if (c.tail_capacity == 0) c.tail_capacity = 1u << 20;
   }
   if (!(c.fs > 0.0) || !std::isfinite(c.fs)) return fail(BEGE_EINVAL, "fs must be positive");
-  if (c.precision != 0) return fail(BEGE_EINVAL, "only precision 0 (FP32) is available");
+  if (c.precision < 0 || c.precision > 2)
+    return fail(BEGE_EINVAL, "precision must be 0 (FP32), 1 (BF16x3) or 2 (FP16x2)");
   if (c.reserved != 0) return fail(BEGE_EINVAL, "reserved must be 0");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -660,6 +661,10 @@ static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
   if (k_begin < 0 || k_end > bank->count || k_begin >= k_end)
     return fail(BEGE_EINVAL, "template range outside the bank or empty");
   if (bank->L > seg->n) return fail(BEGE_EINVAL, "template longer than the segment");
+  if (ctx->cfg.precision != 0 && (seg->n < (1 << 14) || bank->Lp > 4096))
+    return fail(BEGE_EINVAL,
+                "the tensor-core precision form needs N >= 2^14 and templates of at most 4096 "
+                "samples");
   if (!std::isfinite(kappa) && !(dump_dev && std::isinf(kappa)))
     return fail(BEGE_EINVAL, "kappa must be finite");
   if (kappa < 0.f) return fail(BEGE_EINVAL, "kappa must be >= 0");
@@ -675,8 +680,7 @@ static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
   cudaError_t e = cudaEventCreateWithFlags(&job->done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&job->k_start);
   if (e == cudaSuccess) e = cudaEventCreate(&job->k_stop);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(job->buf->counter.ptr, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(job->buf->counter.ptr, 0, 16, s);
   if (e == cudaSuccess) e = cudaEventRecord(job->k_start, s);
   if (e == cudaSuccess) {
     bege::CorrelateArgs a{};
@@ -692,10 +696,15 @@ static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
     a.counter = static_cast<unsigned long long*>(job->buf->counter.ptr);
     a.dump = dump_dev;
     a.max_clusters = 0;
-    auto ci = ctx->configs.find(seg->n);
-    const bege::CorrConfig cc =
-        ci != ctx->configs.end() ? ci->second : bege::default_config(seg->plan->g);
-    e = bege::launch_correlate(seg->plan->dev, a, cc, s);
+    a.status = reinterpret_cast<unsigned int*>(static_cast<char*>(job->buf->counter.ptr) + 8);
+    if (ctx->cfg.precision != 0) {
+      e = bege::launch_correlate_tc(seg->plan->dev, a, ctx->cfg.precision, s);
+    } else {
+      auto ci = ctx->configs.find(seg->n);
+      const bege::CorrConfig cc =
+          ci != ctx->configs.end() ? ci->second : bege::default_config(seg->plan->g);
+      e = bege::launch_correlate(seg->plan->dev, a, cc, s);
+    }
   }
   if (e == cudaSuccess) e = cudaEventRecord(job->k_stop, s);
   if (e == cudaSuccess) e = cudaEventRecord(job->done, s);
@@ -753,9 +762,12 @@ int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capa
   if (!j) return fail(BEGE_EINVAL, "unknown job handle");
   cudaError_t e = cudaEventSynchronize(j->done);
   if (e != cudaSuccess) return cuda_fail(e, "job");
-  unsigned long long total = 0;
-  e = cudaMemcpy(&total, j->buf->counter.ptr, sizeof(total), cudaMemcpyDeviceToHost);
+  unsigned long long cs[2] = {0, 0};
+  e = cudaMemcpy(cs, j->buf->counter.ptr, 16, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "tail count");
+  const unsigned long long total = cs[0];
+  if (cs[1] & 0xffffffffull)
+    return fail(BEGE_ETIMEDOUT, "a bounded device wait gave up; results of this job are invalid");
   uint64_t ncopy = total;
   if (ncopy > j->buf->rec_cap) ncopy = j->buf->rec_cap;
   if (ncopy > (uint64_t)capacity) ncopy = (uint64_t)capacity;

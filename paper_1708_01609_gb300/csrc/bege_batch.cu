@@ -53,12 +53,12 @@ __device__ __forceinline__ void run_item(const BatchArgs& b, const ItemState* st
     // a one-CTA group reads only its own columns: a CTA barrier suffices
     if constexpr (C == 1) __syncthreads(); else cluster.sync();
     if (active) {
-      const float sigma = group_sigma<kF, S, kNC>(gbase, S * 8192);
+      const float sigma = group_sigma<S, kNC>(Smem<kF, kNC>::sigpart(), gbase, S * 8192);
       const int64_t krow = k - st->sg.k0;
       if (grank == 0 && threadIdx.x == 0) st->sg.sigma[krow] = sigma;
       const TailOut out{st->sg.recs, st->sg.cap, st->sg.counter, nullptr};
-      combine_and_emit<kF, S, kNC, kT>(S * 4096, grank, st->sg.kappa * sigma, (uint32_t)k, krow,
-                                       out);
+      combine_and_emit<kF, S, kNC, kT>(Smem<kF, kNC>::colptr(), S * 4096, grank,
+                                       st->sg.kappa * sigma, (uint32_t)k, krow, out);
     }
     if constexpr (C == 1) __syncthreads(); else cluster.sync();
   }

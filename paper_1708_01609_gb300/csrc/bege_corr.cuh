@@ -514,15 +514,13 @@ struct TailOut {
 };
 
 template <int F, int S, int NC, int T>
-__device__ __forceinline__ void combine_and_emit(int H, int rank, float thr, uint32_t tmpl,
-                                                 int64_t krow, const TailOut& a) {
-  using SM = Smem<F, NC>;
+__device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, int rank, float thr,
+                                                 uint32_t tmpl, int64_t krow, const TailOut& a) {
   constexpr int C = ColMap<S, NC>::C;
   constexpr int per = F / C;
   static_assert(per % T == 0, "combine rounds");
   const int lane = threadIdx.x & 31;
   const float invH = 1.0f / (float)H;
-  float2* const* colptr = SM::colptr();
 #pragma unroll 1
   for (int it = 0; it < per / T; ++it) {
     const int n1 = rank * per + it * T + threadIdx.x;
@@ -642,15 +640,14 @@ __device__ __forceinline__ void template_columns(int grank, const float* __restr
 
 // sigma from the sum |Y|^2 partials of the C CTAs of a group (Eq. PT on the
 // packed spectrum: sigma^2 = 2 sum |Y|^2 / N^2).
-template <int F, int S, int NC>
-__device__ __forceinline__ float group_sigma(int gbase, int N) {
-  using SM = Smem<F, NC>;
+template <int S, int NC>
+__device__ __forceinline__ float group_sigma(float* sigpart, int gbase, int N) {
   constexpr int C = ColMap<S, NC>::C;
   cg::cluster_group cluster = cg::this_cluster();
   float tot = 0.f;
 #pragma unroll
   for (int q = 0; q < C; ++q)
-    tot += *cluster.map_shared_rank(SM::sigpart(), (unsigned)(gbase + q));
+    tot += *cluster.map_shared_rank(sigpart, (unsigned)(gbase + q));
   return sqrtf(2.0f * tot) / (float)N;
 }
 
@@ -673,11 +670,12 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
   for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
     template_columns<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold, a.AB);
     cluster.sync();  // every column and every sigma partial of the cluster is ready
-    const float sigma = group_sigma<F, S, NC>(0, N);
+    const float sigma = group_sigma<S, NC>(Smem<F, NC>::sigpart(), 0, N);
     const int64_t krow = k - a.k0;
     if (rank == 0 && threadIdx.x == 0) a.sigma[krow] = sigma;
     // S6: S-point combine, threshold, warp-ballot compaction
-    combine_and_emit<F, S, NC, T>(H, rank, a.kappa * sigma, (uint32_t)k, krow, out);
+    combine_and_emit<F, S, NC, T>(Smem<F, NC>::colptr(), H, rank, a.kappa * sigma, (uint32_t)k,
+                                  krow, out);
     cluster.sync();  // remote reads done before the columns are overwritten
   }
 }

@@ -89,7 +89,8 @@ struct CorrelateArgs {
   uint64_t cap;
   unsigned long long* counter;
   float* dump;
-  int max_clusters;  // 0 = as many as fit
+  int max_clusters;      // 0 = as many as fit
+  unsigned int* status;  // optional: set non-zero by a kernel whose bounded wait gave up
 };
 cudaError_t launch_correlate(const PlanDev& p, const CorrelateArgs& a, CorrConfig cfg,
                              cudaStream_t s);
@@ -105,6 +106,12 @@ cudaError_t launch_correlate_s8(const PlanDev& p, const CorrelateArgs& a, CorrCo
                                 cudaStream_t s);
 cudaError_t launch_correlate_s16(const PlanDev& p, const CorrelateArgs& a, CorrConfig c, bool halfz,
                                  cudaStream_t s);
+
+// Precision form: S2-S6 with the column FFTs on tcgen05 tensor cores.
+// precision 1 = BF16x3, 2 = FP16x2.  Needs F = 4096 (N >= 2^14) and
+// Lp <= 4096.
+cudaError_t launch_correlate_tc(const PlanDev& p, const CorrelateArgs& a, int precision,
+                                cudaStream_t s);
 
 // Bank synthesis: count chirps, phase coefficients alpha/beta as unsigned
 // 64-bit fixed point (cycles * 2^64), L samples, taper fraction; rows of Lp.

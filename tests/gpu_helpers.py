@@ -15,7 +15,7 @@ def make_ctx(**kw):
     return binding.Context(0, **kw)
 
 
-def compare_tails(gpu_recs, ref, kappa, tmpl_subset=None, tol=TOL_FP32):
+def compare_tails(gpu_recs, ref, kappa, tmpl_subset=None, tol=TOL_FP32, near=None):
     """gpu_recs: TAIL_DTYPE records; ref: dict template -> (rho FP64, sigma).
 
     Returns a summary dict; raises AssertionError on a parity violation.
@@ -24,13 +24,14 @@ def compare_tails(gpu_recs, ref, kappa, tmpl_subset=None, tol=TOL_FP32):
         gpu_recs = gpu_recs[np.isin(gpu_recs["tmpl"], np.array(sorted(tmpl_subset), np.uint32))]
     got = {(int(k), int(n)): float(v)
            for k, n, v in zip(gpu_recs["tmpl"], gpu_recs["lag"], gpu_recs["value"])}
+    near_band = NEAR if near is None else near
     n_ref = n_near = 0
     worst = 0.0
     for k, (rho, sig) in ref.items():
         thr = kappa * sig
         lags = np.nonzero(np.abs(rho) > thr)[0]
         for n in lags:
-            near = abs(abs(rho[n]) - thr) <= NEAR * sig
+            near = abs(abs(rho[n]) - thr) <= near_band * sig
             key = (k, int(n))
             if key not in got:
                 assert near, f"missing tail {key}: rho={rho[n]} thr={thr}"
@@ -45,7 +46,7 @@ def compare_tails(gpu_recs, ref, kappa, tmpl_subset=None, tol=TOL_FP32):
                 continue
             if abs(rho[n]) > thr:
                 continue
-            assert abs(abs(rho[n]) - thr) <= NEAR * sig, f"extra tail {(kk, n)}: rho={rho[n]} thr={thr}"
+            assert abs(abs(rho[n]) - thr) <= near_band * sig, f"extra tail {(kk, n)}: rho={rho[n]} thr={thr}"
             n_near += 1
     return {"matched": n_ref, "near": n_near, "worst": worst}
 
