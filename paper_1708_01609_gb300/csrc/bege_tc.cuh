@@ -5,9 +5,14 @@
 //   V[m1][k1] = sum_{m2} u[m1 + 64 m2] w64^(m2 k1)          (GEMM 1)
 //   V'        = V[m1][k1] w4096^(m1 k1)                       (FP32 twiddle)
 //   Z[k1 + 64 k2] = sum_{m1} V'[m1][k1] w64^(m1 k2)           (GEMM 2)
-// A CTA holds the two columns of a unit (b, S-b), so each GEMM is
-// [128 rows] x [128 real K] x [128 real N]: complex values as (re, im)
-// pairs, the 64-point DFT matrix as real 2 x 2 blocks.  The inverse
+// A group of 8 warps holds the two columns of a unit (b, S-b), so each GEMM
+// is [128 rows] x [128 real K] x [128 real N]: complex values as (re, im)
+// pairs, the 64-point DFT matrix as real 2 x 2 blocks.  A kernel that
+// allocates tensor memory runs one CTA per SM, so a CTA carries G = 2 groups
+// (two units, 512 threads) where the transform has S >= 4 columns: each
+// group has its own operands, accumulator (128 TMEM columns) and mbarrier,
+// synchronises on its own named barrier, and one group's MMAs overlap the
+// other's CUDA-core work.  The inverse
 // transform reuses the forward one, IDFT(Y) = conj(DFT(conj(Y))).
 // Operands are split into a high and a low 16-bit part and the GEMM is a sum
 // of products of parts, accumulated in FP32:
@@ -34,9 +39,7 @@ namespace bege {
 namespace tc {
 
 constexpr int kF = 4096;
-constexpr int kNC = 2;
-constexpr int kT = 256;
-constexpr uint32_t kTmemCols = 128;
+constexpr int kGT = 256;  // threads of a group: 8 warps, two per TMEM lane quarter
 
 enum { FP16X2 = 0, BF16X3 = 1 };
 
@@ -59,25 +62,32 @@ struct Part<BF16X3> {
   static __device__ __forceinline__ float back(T h) { return __bfloat162float(h); }
 };
 
-// Shared-memory layout (bytes).
-template <int P>
+// Shared-memory layout (bytes) for G groups of 8 warps, group g holding
+// column slots 2g, 2g+1.  A group's FP32 staging columns and its 16-bit A
+// operand share one region: A is live from a transform's first operand build
+// to the completion of its second GEMM, the columns from there to the end of
+// the product (forward) or of the combine (inverse).  The DFT matrix and the
+// twiddle tables are shared by the groups.
+template <int P, int G>
 struct TcLay {
   static constexpr int CS = col_stride<kF>();
-  static constexpr size_t cols = 0;                               // 2 x CS float2 (FP32)
-  static constexpr size_t a_hi = align16(2 * CS * 8);              // 128 x 128 16-bit
-  static constexpr size_t a_lo = a_hi + 32768;
-  static constexpr size_t b_hi = a_lo + 32768;
-  static constexpr size_t b_lo = b_hi + 32768;                     // BF16x3 only
-  static constexpr size_t w64 = b_lo + (P == BF16X3 ? 32768 : 0);  // w64^k, k < 64
-  static constexpr size_t w4k = w64 + 64 * 8;                      // w4096^k, k < 64
-  static constexpr size_t tin_a = w4k + 64 * 8;                    // [slot][x] wH^(b x)
-  static constexpr size_t tin_b = tin_a + 2 * 64 * 8;              // [slot][x] wH^(64 b x)
-  static constexpr size_t colptr = tin_b + 2 * 64 * 8;
-  static constexpr size_t red = colptr + 16 * 8;
-  static constexpr size_t sigpart = red + 32 * 4;
-  static constexpr size_t mbar = sigpart + 16;
-  static constexpr size_t tslot = mbar + 8;
+  static constexpr size_t R = 2 * CS * 8;                           // one group's region
+  static_assert(R >= 65536 && R % 128 == 0, "region holds A_hi and A_lo");
+  static constexpr size_t cols = 0;                                 // slot s at s * CS float2
+  static constexpr size_t b_hi = G * R;                             // 128 x 128 16-bit
+  static constexpr size_t b_lo = b_hi + 32768;                      // BF16x3 only
+  static constexpr size_t w64 = b_lo + (P == BF16X3 ? 32768 : 0);   // w64^k, k < 64
+  static constexpr size_t w4k = w64 + 64 * 8;                       // w4096^k, k < 64
+  static constexpr size_t tin_a = w4k + 64 * 8;                     // [slot][x] wH^(b x)
+  static constexpr size_t tin_b = tin_a + 2 * G * 64 * 8;           // [slot][x] wH^(64 b x)
+  static constexpr size_t colptr = tin_b + 2 * G * 64 * 8;
+  static constexpr size_t red = colptr + 16 * 8;                    // [group][32]
+  static constexpr size_t sigpart = red + G * 32 * 4;               // [group]
+  static constexpr size_t mbar = sigpart + 16;                      // [group]
+  static constexpr size_t tslot = mbar + 8 * G;
   static constexpr size_t total = tslot + 8;
+  static __host__ __device__ constexpr size_t a_hi(int g) { return g * R; }
+  static __host__ __device__ constexpr size_t a_lo(int g) { return g * R + 32768; }
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -163,19 +173,18 @@ __device__ __forceinline__ void store_split8(unsigned char* hi, unsigned char* l
   *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(l);
 }
 
-template <int P>
+template <int P, int G>
 struct Smem {
-  using L = TcLay<P>;
-  static __device__ __forceinline__ float2* col(int c) {
-    return reinterpret_cast<float2*>(smem_raw + L::cols) + c * L::CS;
+  using L = TcLay<P, G>;
+  static __device__ __forceinline__ float2* col(int slot) {
+    return reinterpret_cast<float2*>(smem_raw + L::cols) + slot * L::CS;
   }
-  static __device__ __forceinline__ unsigned char* base() { return smem_raw; }
   static __device__ __forceinline__ float2* w64() { return reinterpret_cast<float2*>(smem_raw + L::w64); }
   static __device__ __forceinline__ float2* w4k() { return reinterpret_cast<float2*>(smem_raw + L::w4k); }
   static __device__ __forceinline__ float2* tin_a() { return reinterpret_cast<float2*>(smem_raw + L::tin_a); }
   static __device__ __forceinline__ float2* tin_b() { return reinterpret_cast<float2*>(smem_raw + L::tin_b); }
   static __device__ __forceinline__ float2** colptr() { return reinterpret_cast<float2**>(smem_raw + L::colptr); }
-  static __device__ __forceinline__ float* red() { return reinterpret_cast<float*>(smem_raw + L::red); }
+  static __device__ __forceinline__ float* red(int g) { return reinterpret_cast<float*>(smem_raw + L::red) + 32 * g; }
   static __device__ __forceinline__ float* sigpart() { return reinterpret_cast<float*>(smem_raw + L::sigpart); }
 };
 
@@ -186,18 +195,17 @@ __device__ __forceinline__ float2 root(int64_t k, int64_t M) {
 }
 
 // w4096^p for p < 4096 from the two 64-entry tables: w64^(p/64) w4096^(p%64).
-template <int P>
+template <int P, int G>
 __device__ __forceinline__ float2 w4096(int p) {
-  return cmul(Smem<P>::w64()[p >> 6], Smem<P>::w4k()[p & 63]);
+  return cmul(Smem<P, G>::w64()[p >> 6], Smem<P, G>::w4k()[p & 63]);
 }
 
 // Issue one GEMM: D = sum of the part products over K (K = 64 or 128), then
-// commit to the mbarrier.  Thread 0 only.
+// commit to the mbarrier.  One thread of the group.  ah, al: the group's A
+// parts; bh, bl: the DFT matrix parts (shared-memory addresses).
 template <int P>
-__device__ __forceinline__ void issue_gemm(uint32_t tmem, bool a_mn, int K, uint32_t mbar) {
-  using L = TcLay<P>;
-  const uint32_t base = smem_addr(smem_raw);
-  const uint32_t ah = base + L::a_hi, al = base + L::a_lo, bh = base + L::b_hi, bl = base + L::b_lo;
+__device__ __forceinline__ void issue_gemm(uint32_t tmem, uint32_t ah, uint32_t al, uint32_t bh,
+                                           uint32_t bl, bool a_mn, int K, uint32_t mbar) {
   // K-major A: LBO 128 (along K), SBO 2048 (along rows); MN-major A: LBO 2048, SBO 128
   const uint32_t a_lbo = a_mn ? 2048u : 128u, a_sbo = a_mn ? 128u : 2048u;
   const uint32_t a_step = a_mn ? 4096u : 256u;  // 16 K = two core matrices along K
