@@ -520,7 +520,10 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
   constexpr int per = F / C;
   static_assert(per % T == 0, "combine rounds");
   const int lane = threadIdx.x & 31;
+  // rho = t / H with H a power of two: |t / H| > thr exactly when |t| > thr H,
+  // so the unscaled values are tested and only the emitted ones are scaled
   const float invH = 1.0f / (float)H;
+  const float thrH = thr * (float)H;
 #pragma unroll 1
   for (int it = 0; it < per / T; ++it) {
     const int n1 = rank * per + it * T + threadIdx.x;
@@ -529,19 +532,21 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
 #pragma unroll
     for (int b = 0; b < S; ++b) t[b] = colptr[b][pn1];
     dft<S, true>(t);
-    uint32_t mask = 0;
+    float big = 0.f;
 #pragma unroll
-    for (int n2 = 0; n2 < S; ++n2) {
-      t[n2] = cscale(t[n2], invH);
-      mask |= (fabsf(t[n2].x) > thr ? 1u : 0u) << (2 * n2);
-      mask |= (fabsf(t[n2].y) > thr ? 1u : 0u) << (2 * n2 + 1);
-    }
+    for (int n2 = 0; n2 < S; ++n2) big = fmaxf(big, fmaxf(fabsf(t[n2].x), fabsf(t[n2].y)));
     if (a.dump) {
       float2* row = reinterpret_cast<float2*>(a.dump) + krow * (int64_t)H;
 #pragma unroll
-      for (int n2 = 0; n2 < S; ++n2) row[n1 + F * n2] = t[n2];
+      for (int n2 = 0; n2 < S; ++n2) row[n1 + F * n2] = cscale(t[n2], invH);
     }
-    if (__any_sync(0xffffffffu, mask != 0u)) {
+    if (__any_sync(0xffffffffu, big > thrH)) {
+      uint32_t mask = 0;
+#pragma unroll
+      for (int n2 = 0; n2 < S; ++n2) {
+        mask |= (fabsf(t[n2].x) > thrH ? 1u : 0u) << (2 * n2);
+        mask |= (fabsf(t[n2].y) > thrH ? 1u : 0u) << (2 * n2 + 1);
+      }
       const int cnt = __popc(mask);
       int incl = cnt;
 #pragma unroll
@@ -563,7 +568,7 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
               bege_tail* r = a.recs + pos;
               r->tmpl = tmpl;
               r->lag = (uint32_t)(2 * (n1 + F * n2) + e);
-              r->value = e ? t[n2].y : t[n2].x;
+              r->value = (e ? t[n2].y : t[n2].x) * invH;
             }
             ++pos;
           }

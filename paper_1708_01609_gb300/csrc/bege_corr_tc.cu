@@ -182,6 +182,8 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
     // ---- forward GEMM 1 operand: u_c[m1 + 64 m2] = wH^(b m) z[m], K-major;
     // the twiddles of a run of 8 m2 from one product and the step wH^(64 b)
     const float2* z = reinterpret_cast<const float2*>(a.bank + k * a.Lp);
+    if (k + ncl < a.k1 && tid * 32 < a.Lp)  // the next template's samples to L2
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.bank + (k + ncl) * a.Lp + tid * 32));
     float ure[2][8], uim[2][8];
     float umax = 0.f;
 #pragma unroll
@@ -243,7 +245,39 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
     // ---- S3 + S4 in FP32: Y = conj(Z) A + Z' B over the unit's bin pairs,
     // in place; four items' loads are issued before their arithmetic
     float acc = 0.f, ymax = 0.f;
-    {
+    if (ug != 0) {
+      // unit {b, S-b}: pairs (a, F-1-a) of slots 2g, 2g+1, all distinct
+      const int b = ug, bp = S - ug;
+      float2* c0 = SM::col(2 * g);
+      float2* c1 = SM::col(2 * g + 1);
+#pragma unroll 1
+      for (int it0 = 0; it0 < kF; it0 += 4 * kGT) {
+        float2 zj[4], zp[4];
+        float4 abj[4], abp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int it = it0 + u * kGT + lt, ip = kF - 1 - it;
+          abj[u] = __ldcg(a.AB + b * kF + it);
+          abp[u] = __ldcg(a.AB + bp * kF + ip);
+          zj[u] = c0[pad(it)];
+          zp[u] = c1[pad(ip)];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int it = it0 + u * kGT + lt, ip = kF - 1 - it;
+          const float2 yj = cadd(cconjmul(zj[u], make_float2(abj[u].x, abj[u].y)),
+                                 cmul(zp[u], make_float2(abj[u].z, abj[u].w)));
+          const float2 yp = cadd(cconjmul(zp[u], make_float2(abp[u].x, abp[u].y)),
+                                 cmul(zj[u], make_float2(abp[u].z, abp[u].w)));
+          acc = fmaf(yj.x, yj.x, fmaf(yj.y, yj.y, acc));
+          acc = fmaf(yp.x, yp.x, fmaf(yp.y, yp.y, acc));
+          ymax = fmaxf(ymax, fmaxf(fmaxf(fabsf(yj.x), fabsf(yj.y)), fmaxf(fabsf(yp.x), fabsf(yp.y))));
+          c0[pad(it)] = yj;
+          c1[pad(ip)] = yp;
+        }
+      }
+    } else {
+      // unit {0, S/2}: each column pairs with itself
       const int count = unit_items<kF, S>(ug);
       for (int it0 = 0; it0 < count; it0 += 4 * kGT) {
         float2 zj[4], zp[4];
