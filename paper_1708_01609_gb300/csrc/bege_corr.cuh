@@ -515,7 +515,8 @@ struct TailOut {
 
 template <int F, int S, int NC, int T>
 __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, int rank, float thr,
-                                                 uint32_t tmpl, int64_t krow, const TailOut& a) {
+                                                 uint32_t tmpl, int64_t krow, const TailOut& a,
+                                                 int tix = threadIdx.x) {
   constexpr int C = ColMap<S, NC>::C;
   constexpr int per = F / C;
   static_assert(per % T == 0, "combine rounds");
@@ -526,7 +527,7 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
   const float thrH = thr * (float)H;
 #pragma unroll 1
   for (int it = 0; it < per / T; ++it) {
-    const int n1 = rank * per + it * T + threadIdx.x;
+    const int n1 = rank * per + it * T + tix;
     const int pn1 = pad(n1);
     float2 t[S];
 #pragma unroll

@@ -157,20 +157,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Split 8 complex values into the high/low 16-bit parts of their (re, im)
-// and store them as 16-byte runs (8 consecutive K or rows) of part `part`.
+// Split 8 FP32 values into their high and low 16-bit parts, hi = rn(x),
+// lo = rn(x - hi), converting two values per instruction, and store each
+// part as one 16-byte run (8 consecutive K or rows).
 template <int P>
 __device__ __forceinline__ void store_split8(unsigned char* hi, unsigned char* lo, uint32_t off,
                                              const float (&x)[8]) {
-  using PT = Part<P>;
-  typename PT::T h[8], l[8];
+  uint32_t h[4], l[4];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    h[e] = PT::cvt(x[e]);
-    l[e] = PT::cvt(x[e] - PT::back(h[e]));
+  for (int e = 0; e < 4; ++e) {
+    if constexpr (P == FP16X2) {
+      const __half2 hh = __floats2half2_rn(x[2 * e], x[2 * e + 1]);
+      const float2 bk = __half22float2(hh);
+      const __half2 ll = __floats2half2_rn(x[2 * e] - bk.x, x[2 * e + 1] - bk.y);
+      h[e] = *reinterpret_cast<const uint32_t*>(&hh);
+      l[e] = *reinterpret_cast<const uint32_t*>(&ll);
+    } else {
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+      const float2 bk = __bfloat1622float2(hh);
+      const __nv_bfloat162 ll = __floats2bfloat162_rn(x[2 * e] - bk.x, x[2 * e + 1] - bk.y);
+      h[e] = *reinterpret_cast<const uint32_t*>(&hh);
+      l[e] = *reinterpret_cast<const uint32_t*>(&ll);
+    }
   }
-  *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<const uint4*>(h);
-  *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<const uint4*>(l);
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 template <int P, int G>
