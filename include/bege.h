@@ -51,7 +51,7 @@ typedef struct {
   double fs;                  /* sample rate in Hz (the paper: 4096, Sec. 3)     */
   uint64_t hbm_budget_bytes;  /* cap on library-owned device memory; 0 = none    */
   uint64_t tail_capacity;     /* device tail records per job; 0 = 1<<20          */
-  int32_t precision;          /* 0 = FP32; 1 = BF16x3, 2 = FP16x2: the precision
+  int32_t precision;          /* 0 = FP32; 1 = BF16x3, 2 = FP16x3: the precision
                                  form, column FFTs on tensor cores with split
                                  (hi + lo) 16-bit operands, FP32 accumulation
                                  (needs N >= 2^14, templates <= 4096 samples) */

@@ -485,7 +485,7 @@ int bege_create(bege_ctx** out, int device, const bege_config* cfg) {
   }
   if (!(c.fs > 0.0) || !std::isfinite(c.fs)) return fail(BEGE_EINVAL, "fs must be positive");
   if (c.precision < 0 || c.precision > 2)
-    return fail(BEGE_EINVAL, "precision must be 0 (FP32), 1 (BF16x3) or 2 (FP16x2)");
+    return fail(BEGE_EINVAL, "precision must be 0 (FP32), 1 (BF16x3) or 2 (FP16x3)");
   if (c.reserved != 0) return fail(BEGE_EINVAL, "reserved must be 0");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);

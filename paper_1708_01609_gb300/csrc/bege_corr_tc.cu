@@ -157,9 +157,8 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
     using PT = Part<P>;
     const typename PT::T hv = PT::cvt(v);
     *reinterpret_cast<typename PT::T*>(smem_raw + L::b_hi + off_kmajor(n, K)) = hv;
-    if (P == BF16X3)
-      *reinterpret_cast<typename PT::T*>(smem_raw + L::b_lo + off_kmajor(n, K)) =
-          PT::cvt(v - PT::back(hv));
+    *reinterpret_cast<typename PT::T*>(smem_raw + L::b_lo + off_kmajor(n, K)) =
+        PT::cvt(v - PT::back(hv));
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -207,13 +206,13 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
         umax = fmaxf(umax, fmaxf(fabsf(v.x), fabsf(v.y)));
       }
     }
-    float su = 1.f;  // FP16x2: scale of the forward operand
-    if constexpr (P == FP16X2) su = pow2_scale(group_max(g, umax, red + 16));
+    float su = 1.f;  // FP16x3: scale of the forward operand
+    if constexpr (P == FP16X3) su = pow2_scale(group_max(g, umax, red + 16));
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int u = lt + i * kGT;
       const int m1 = u & 63, blk = (u >> 6) & 3, c = u >> 8;
-      if constexpr (P == FP16X2) {
+      if constexpr (P == FP16X3) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           ure[i][e] *= su;
@@ -317,8 +316,8 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
     }
     acc = warp_sum(acc);
     if (lane == 0) red[warp & 7] = acc;
-    float sy = 1.f;  // FP16x2: scale of the inverse operand
-    if constexpr (P == FP16X2)
+    float sy = 1.f;  // FP16x3: scale of the inverse operand
+    if constexpr (P == FP16X3)
       sy = pow2_scale(group_max(g, ymax, red + 16));
     else
       group_sync(g);
@@ -445,10 +444,10 @@ cudaError_t launch_correlate_tc(const PlanDev& p, const CorrelateArgs& a, int pr
   if (a.k1 <= a.k0) return cudaSuccess;
   const bool bf = precision == 1;
   switch (p.g.S) {
-    case 2: return bf ? tc::launch_tc_t<2, tc::BF16X3, 1>(p, a, s) : tc::launch_tc_t<2, tc::FP16X2, 1>(p, a, s);
-    case 4: return bf ? tc::launch_tc_t<4, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<4, tc::FP16X2, 2>(p, a, s);
-    case 8: return bf ? tc::launch_tc_t<8, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<8, tc::FP16X2, 2>(p, a, s);
-    case 16: return bf ? tc::launch_tc_t<16, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<16, tc::FP16X2, 2>(p, a, s);
+    case 2: return bf ? tc::launch_tc_t<2, tc::BF16X3, 1>(p, a, s) : tc::launch_tc_t<2, tc::FP16X3, 1>(p, a, s);
+    case 4: return bf ? tc::launch_tc_t<4, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<4, tc::FP16X3, 2>(p, a, s);
+    case 8: return bf ? tc::launch_tc_t<8, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<8, tc::FP16X3, 2>(p, a, s);
+    case 16: return bf ? tc::launch_tc_t<16, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<16, tc::FP16X3, 2>(p, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -108,7 +108,7 @@ cudaError_t launch_correlate_s16(const PlanDev& p, const CorrelateArgs& a, CorrC
                                  cudaStream_t s);
 
 // Precision form: S2-S6 with the column FFTs on tcgen05 tensor cores.
-// precision 1 = BF16x3, 2 = FP16x2.  Needs F = 4096 (N >= 2^14) and
+// precision 1 = BF16x3, 2 = FP16x3.  Needs F = 4096 (N >= 2^14) and
 // Lp <= 4096.
 cudaError_t launch_correlate_tc(const PlanDev& p, const CorrelateArgs& a, int precision,
                                 cudaStream_t s);

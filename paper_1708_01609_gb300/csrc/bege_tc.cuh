@@ -16,8 +16,12 @@
 // transform reuses the forward one, IDFT(Y) = conj(DFT(conj(Y))).
 // Operands are split into a high and a low 16-bit part and the GEMM is a sum
 // of products of parts, accumulated in FP32:
-//   FP16x2: A_hi B_hi + A_lo B_hi   (the DFT matrix rounded to FP16 once)
 //   BF16x3: A_hi B_hi + A_lo B_hi + A_hi B_lo
+//   FP16x3: the same three products in FP16 (three more mantissa bits than
+//           BF16, far less range: each transform's input is scaled by a power
+//           of two into FP16's range and the output scaled back, exactly)
+// Two terms (an FP16 DFT matrix without its low part) are not enough: on
+// narrowband chirps its rounding alone exceeds 2e-3 sigma.
 // Twiddles, the spectral product, the Parseval sum and the S-point combine
 // stay in FP32 (the single-segment kernel's arithmetic).
 //
@@ -41,15 +45,15 @@ namespace tc {
 constexpr int kF = 4096;
 constexpr int kGT = 256;  // threads of a group: 8 warps, two per TMEM lane quarter
 
-enum { FP16X2 = 0, BF16X3 = 1 };
+enum { FP16X3 = 0, BF16X3 = 1 };
 
 template <int P>
 struct Part;
 template <>
-struct Part<FP16X2> {
+struct Part<FP16X3> {
   using T = __half;
   static constexpr uint32_t fmt = 0;
-  static constexpr int terms = 2;
+  static constexpr int terms = 3;
   static __device__ __forceinline__ T cvt(float x) { return __float2half_rn(x); }
   static __device__ __forceinline__ float back(T h) { return __half2float(h); }
 };
@@ -75,8 +79,8 @@ struct TcLay {
   static_assert(R >= 65536 && R % 128 == 0, "region holds A_hi and A_lo");
   static constexpr size_t cols = 0;                                 // slot s at s * CS float2
   static constexpr size_t b_hi = G * R;                             // 128 x 128 16-bit
-  static constexpr size_t b_lo = b_hi + 32768;                      // BF16x3 only
-  static constexpr size_t w64 = b_lo + (P == BF16X3 ? 32768 : 0);   // w64^k, k < 64
+  static constexpr size_t b_lo = b_hi + 32768;
+  static constexpr size_t w64 = b_lo + 32768;                       // w64^k, k < 64
   static constexpr size_t w4k = w64 + 64 * 8;                       // w4096^k, k < 64
   static constexpr size_t tin_a = w4k + 64 * 8;                     // [slot][x] wH^(b x)
   static constexpr size_t tin_b = tin_a + 2 * G * 64 * 8;           // [slot][x] wH^(64 b x)
@@ -166,7 +170,7 @@ __device__ __forceinline__ void store_split8(unsigned char* hi, unsigned char* l
   uint32_t h[4], l[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    if constexpr (P == FP16X2) {
+    if constexpr (P == FP16X3) {
       const __half2 hh = __floats2half2_rn(x[2 * e], x[2 * e + 1]);
       const float2 bk = __half22float2(hh);
       const __half2 ll = __floats2half2_rn(x[2 * e] - bk.x, x[2 * e + 1] - bk.y);
