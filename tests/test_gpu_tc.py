@@ -153,3 +153,59 @@ def test_tc_paper_scale_tails_match_fp32_path(prec):
     assert len(both) > 1e6
     assert np.all(err <= TOL_TC)
     assert np.all(dist <= TOL_TC)
+
+
+def _sorted(recs):
+    key = recs["tmpl"].astype(np.int64) << 32 | recs["lag"].astype(np.int64)
+    return recs[np.argsort(key)]
+
+
+def test_tc_subrange_equals_full_run(tctx):
+    """Each template is computed on its own: a range [k0, k1) of the bank
+    gives bitwise the records and sigma of those rows in a full run, and a
+    repeated run is bitwise the same."""
+    prec, ctx = tctx
+    seg_data, params = S.small_case()
+    seg = ctx.bege_load_segment(seg_data.y)
+    bid = ctx.bege_define_bank(params)
+    full = ctx.bege_correlate(seg, bid, 0, len(params), 4.0)
+    r_full, _ = ctx.bege_fetch_tails(full)
+    s_full = ctx.bege_get_sigma(full, len(params))
+    again = ctx.bege_correlate(seg, bid, 0, len(params), 4.0)
+    r_again, _ = ctx.bege_fetch_tails(again)
+    assert np.array_equal(_sorted(r_full), _sorted(r_again))
+    k0, k1 = 5, 37
+    part = ctx.bege_correlate(seg, bid, k0, k1, 4.0)
+    r_part, _ = ctx.bege_fetch_tails(part)
+    s_part = ctx.bege_get_sigma(part, k1 - k0)
+    sel = r_full[(r_full["tmpl"] >= k0) & (r_full["tmpl"] < k1)]
+    assert len(sel) > 0
+    assert np.array_equal(_sorted(sel), _sorted(r_part))
+    assert np.array_equal(s_full[k0:k1], s_part)
+    from paper_1708_01609_gb300.binding import BegeError
+    with pytest.raises(BegeError):
+        ctx.bege_correlate(seg, bid, 7, 7, 4.0)  # an empty range is an argument error
+    for h in (full, again, part, bid, seg):
+        ctx.bege_release(h)
+
+
+def test_tc_tail_overflow_keeps_count():
+    """A device tail buffer smaller than the tails: the true count is
+    returned and the records kept are real tails of the full set."""
+    seg_data, params = S.small_case()
+    c = make_ctx(tail_capacity=64, precision=1)
+    seg = c.bege_load_segment(seg_data.y)
+    bid = c.bege_define_bank(params)
+    job = c.bege_correlate(seg, bid, 0, len(params), 4.0)
+    recs, total = c.bege_fetch_tails(job, capacity=64)
+    c.close()
+    big = make_ctx(tail_capacity=1 << 20, precision=1)
+    seg = big.bege_load_segment(seg_data.y)
+    bid = big.bege_define_bank(params)
+    job = big.bege_correlate(seg, bid, 0, len(params), 4.0)
+    allrecs, total_all = big.bege_fetch_tails(job)
+    big.close()
+    assert total == total_all > 64
+    assert len(recs) == 64
+    keys = set(zip(allrecs["tmpl"].tolist(), allrecs["lag"].tolist()))
+    assert all((int(t), int(l)) in keys for t, l in zip(recs["tmpl"], recs["lag"]))
