@@ -34,33 +34,43 @@ struct ItemState {
   int64_t k_begin, k_end;
 };
 
-template <int S>
+// One work item.  The per-template body takes the column count S = N/8192
+// at run time, so a single copy of it serves every segment length; only the
+// S-point combine is compiled per S.  (With four per-S copies of the body the
+// kernel spills about 1 KB per thread under its 128-register budget.)
 __device__ __forceinline__ void run_item(const BatchArgs& b, const ItemState* st, int rank) {
-  constexpr int C = ColMap<S, kNC>::C;
-  constexpr int G = kCluster / C;
+  const int S = st->sg.S;
+  const int C = S / kNC;
+  const int G = kCluster / C;
   cg::cluster_group cluster = cg::this_cluster();
   const int group = rank / C, grank = rank - group * C, gbase = group * C;
   const PlanDev& p = b.plans[plan_index(S)];
-  setup_columns<kF, S, kNC, kT>(p, grank, gbase, true);
+  setup_columns<kF, 0, kNC, kT>(p, grank, gbase, true, S);
   __syncthreads();
   const int64_t iters = (st->k_end - st->k_begin + G - 1) / G;
   for (int64_t i = 0; i < iters; ++i) {
     const int64_t k = st->k_begin + i * G + group;
     const bool active = k < st->k_end;  // uniform over the CTAs of a group
     if (active)
-      template_columns<kF, S, kNC, kT, true>(grank, st->sg.bank + k * st->sg.Lp,
-                                             (int)(st->sg.Lp / 2), 1, st->sg.AB);
+      template_columns<kF, 0, kNC, kT, true>(grank, st->sg.bank + k * st->sg.Lp,
+                                             (int)(st->sg.Lp / 2), 1, st->sg.AB, S);
     // a one-CTA group reads only its own columns: a CTA barrier suffices
-    if constexpr (C == 1) __syncthreads(); else cluster.sync();
+    if (C == 1) __syncthreads(); else cluster.sync();
     if (active) {
-      const float sigma = group_sigma<S, kNC>(Smem<kF, kNC>::sigpart(), gbase, S * 8192);
+      const float sigma = group_sigma_rt(Smem<kF, kNC>::sigpart(), gbase, C, S * 8192);
       const int64_t krow = k - st->sg.k0;
       if (grank == 0 && threadIdx.x == 0) st->sg.sigma[krow] = sigma;
       const TailOut out{st->sg.recs, st->sg.cap, st->sg.counter, nullptr};
-      combine_and_emit<kF, S, kNC, kT>(Smem<kF, kNC>::colptr(), S * 4096, grank,
-                                       st->sg.kappa * sigma, (uint32_t)k, krow, out);
+      const float thr = st->sg.kappa * sigma;
+      float2* const* cp = Smem<kF, kNC>::colptr();
+      switch (S) {
+        case 2: combine_and_emit<kF, 2, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out); break;
+        case 4: combine_and_emit<kF, 4, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out); break;
+        case 8: combine_and_emit<kF, 8, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out); break;
+        default: combine_and_emit<kF, 16, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out); break;
+      }
     }
-    if constexpr (C == 1) __syncthreads(); else cluster.sync();
+    if (C == 1) __syncthreads(); else cluster.sync();
   }
 }
 
@@ -83,12 +93,7 @@ __global__ void __launch_bounds__(kT, 2) batch_kernel(BatchArgs b) {
       st.k_end = item.k_end;
     }
     __syncthreads();
-    switch (st.sg.S) {
-      case 2: run_item<2>(b, &st, rank); break;
-      case 4: run_item<4>(b, &st, rank); break;
-      case 8: run_item<8>(b, &st, rank); break;
-      default: run_item<16>(b, &st, rank); break;
-    }
+    run_item(b, &st, rank);
   }
 }
 

@@ -90,6 +90,32 @@ struct Smem {
   static __device__ __forceinline__ float* sigpart() { return reinterpret_cast<float*>(smem_raw + L::sigpart); }
 };
 
+// Column ownership for S >= 2 columns split over S/NC CTAs, S given at run
+// time: unit u (u < S/2) holds columns u and S-u, unit 0 columns 0 and S/2;
+// a CTA holds NC/2 consecutive units.
+template <int NC>
+__device__ __forceinline__ int slot_column_rt(int S, int rank, int c) {
+  const int ug = rank * (NC / 2) + (c >> 1);
+  const int second = c & 1;
+  if (ug == 0) return second ? S / 2 : 0;
+  return second ? S - ug : ug;
+}
+template <int NC>
+__device__ __forceinline__ void home_rt(int S, int b, int* owner, int* slot) {
+  int unit, second;
+  if (b == 0) {
+    unit = 0; second = 0;
+  } else if (b == S / 2) {
+    unit = 0; second = 1;
+  } else if (b < S / 2) {
+    unit = b; second = 0;
+  } else {
+    unit = S - b; second = 1;
+  }
+  *owner = unit / (NC / 2);
+  *slot = 2 * (unit % (NC / 2)) + second;
+}
+
 // Column ownership for S columns split over C = S/NC CTAs.
 template <int S, int NC>
 struct ColMap {
@@ -98,14 +124,10 @@ struct ColMap {
   static constexpr int UPC = S == 1 ? 1 : NC / 2;
   // column b held by local slot c of the CTA with cluster rank `rank`
   static __device__ __forceinline__ int slot_column(int rank, int c) {
-    if constexpr (S == 1) {
+    if constexpr (S == 1)
       return 0;
-    } else {
-      const int ug = rank * UPC + (c >> 1);
-      const int second = c & 1;
-      if (ug == 0) return second ? S / 2 : 0;
-      return second ? S - ug : ug;
-    }
+    else
+      return slot_column_rt<NC>(S, rank, c);
   }
   // owner rank and local slot of column b
   static __device__ __forceinline__ void home(int b, int* owner, int* slot) {
@@ -113,21 +135,21 @@ struct ColMap {
       *owner = 0;
       *slot = 0;
     } else {
-      int unit, second;
-      if (b == 0) {
-        unit = 0; second = 0;
-      } else if (b == S / 2) {
-        unit = 0; second = 1;
-      } else if (b < S / 2) {
-        unit = b; second = 0;
-      } else {
-        unit = S - b; second = 1;
-      }
-      *owner = unit / UPC;
-      *slot = 2 * (unit % UPC) + second;
+      home_rt<NC>(S, b, owner, slot);
     }
   }
 };
+
+// The functions below take the column count S as a template argument; S = 0
+// means "given at run time" (argument s_rt, S >= 2), which lets one kernel
+// body serve every segment length with the same arithmetic.
+template <int S, int NC>
+__device__ __forceinline__ int slot_col(int s_rt, int rank, int c) {
+  if constexpr (S == 1)
+    return 0;
+  else
+    return slot_column_rt<NC>(S ? S : s_rt, rank, c);
+}
 
 // Twiddle tables that depend on F only (the Stockham passes).
 template <int F, int NC, int T>
@@ -141,24 +163,30 @@ __device__ void setup_common(const PlanDev& p) {
 // C = S/NC CTAs) and the (possibly remote) address of every column of the
 // group, whose first CTA has cluster rank `gbase`.
 template <int F, int S, int NC, int T>
-__device__ void setup_columns(const PlanDev& p, int grank, int gbase, bool map_columns) {
+__device__ void setup_columns(const PlanDev& p, int grank, int gbase, bool map_columns,
+                              int s_rt = S) {
   using SM = Smem<F, NC>;
-  using CM = ColMap<S, NC>;
+  const int Sv = S ? S : s_rt;
   const int t = threadIdx.x;
   for (int i = t; i < NC * 256; i += T) {
     const int c = i >> 8, j = i & 255;
-    SM::twin()[i] = p.wH[CM::slot_column(grank, c) * j];
+    SM::twin()[i] = p.wH[slot_col<S, NC>(Sv, grank, c) * j];
   }
   for (int i = t; i < NC * 16; i += T) {
     const int c = i >> 4, r = i & 15;
-    const int b = CM::slot_column(grank, c);
+    const int b = slot_col<S, NC>(Sv, grank, c);
     SM::rin()[i] = r < F / 256 ? p.wR0S[b * r] : make_float2(1.f, 0.f);
     SM::rout()[i] = cconj(p.w16S[b * r]);
   }
-  if (t < 16) SM::ws()[t] = t < S ? p.wS[t] : make_float2(1.f, 0.f);
-  if (map_columns && t < S) {
+  if (t < 16) SM::ws()[t] = t < Sv ? p.wS[t] : make_float2(1.f, 0.f);
+  if (map_columns && t < Sv) {
     int owner, slot;
-    CM::home(t, &owner, &slot);
+    if constexpr (S == 1) {
+      owner = 0;
+      slot = 0;
+    } else {
+      home_rt<NC>(Sv, t, &owner, &slot);
+    }
     cg::cluster_group cl = cg::this_cluster();
     float2* base = cl.map_shared_rank(SM::cols(), (unsigned)(gbase + owner));
     SM::colptr()[t] = base + slot * col_stride<F>();
@@ -171,9 +199,9 @@ __device__ void setup_columns(const PlanDev& p, int grank, int gbase, bool map_c
 // and the upper half of every radix-16 input vector is zero.
 template <int F, int S, int NC, int T, bool HALFZ>
 __device__ __forceinline__ void fwd_first_pass(int rank, const float* __restrict__ src, int nz,
-                                               int nfold) {
+                                               int nfold, int s_rt = S) {
   using SM = Smem<F, NC>;
-  using CM = ColMap<S, NC>;
+  const int Sv = S ? S : s_rt;
   constexpr int R0 = F / 256;
   constexpr int RL = HALFZ ? R0 / 2 : R0;  // inputs that can be non-zero
   constexpr int total = NC * 256;
@@ -191,16 +219,16 @@ __device__ __forceinline__ void fwd_first_pass(int rank, const float* __restrict
         if (r < RL) {
           if (m1 < nz) acc = __ldg(z + m1);
           if (!HALFZ && nfold > 1) {
-            const int b = CM::slot_column(rank, c);
+            const int b = slot_col<S, NC>(Sv, rank, c);
             for (int m2 = 1; m2 < nfold; ++m2) {
               const int m = m1 + F * m2;
-              if (m < nz) acc = cadd(acc, cmul(__ldg(z + m), SM::ws()[(b * m2) & (S - 1)]));
+              if (m < nz) acc = cadd(acc, cmul(__ldg(z + m), SM::ws()[(b * m2) & (Sv - 1)]));
             }
           }
         }
         v[r] = acc;
       }
-      if constexpr (S > 1) {
+      if constexpr (S != 1) {
         const float2 tj = SM::twin()[c * 256 + j];
         const float2* rin = SM::rin() + c * 16;
 #pragma unroll
@@ -240,7 +268,7 @@ __device__ __forceinline__ void inv_last_pass() {
 #pragma unroll
       for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], t3[r * Ns]);
       dft<16, true>(v);
-      if constexpr (S > 1) {
+      if constexpr (S != 1) {
         const float2 tk = SM::twin()[c * 256 + j];
         const float2* ro = SM::rout() + c * 16;
 #pragma unroll
@@ -333,12 +361,12 @@ __device__ __forceinline__ float warp_sum(float v) {
 // ---------------------------------------------------------------------------
 template <int S, int NC, int T>
 __device__ __forceinline__ float fused_mid(int rank, const float4* __restrict__ AB,
-                                           float* red_warp) {
+                                           float* red_warp, int s_rt = S) {
   constexpr int F = 4096;
   using SM = Smem<F, NC>;
-  using CM = ColMap<S, NC>;
-  constexpr int UPC = CM::UPC;
+  constexpr int UPC = S == 1 ? 1 : NC / 2;
   constexpr int items = S == 1 ? 128 : 256;  // per unit
+  const int Sv = S ? S : s_rt;
   static_assert(T >= items * UPC, "one item per thread");
   constexpr int step = 256 + 16;             // padded distance of rows r -> r + 1
   const int t = threadIdx.x;
@@ -353,10 +381,10 @@ __device__ __forceinline__ float fused_mid(int rank, const float4* __restrict__ 
     ja = it; jb = it == 0 ? 128 : 256 - it;
     self0 = (it == 0);
   } else if (ug == 0) {
-    sa = sb = 2 * ui + 1; ba = bb = S / 2;
+    sa = sb = 2 * ui + 1; ba = bb = Sv / 2;
     ja = it - 128; jb = 255 - ja;
   } else {
-    sa = 2 * ui; sb = 2 * ui + 1; ba = ug; bb = S - ug;
+    sa = 2 * ui; sb = 2 * ui + 1; ba = ug; bb = Sv - ug;
     ja = it; jb = 255 - it;
   }
   float2 za[16], zb[16];
@@ -584,16 +612,17 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
 // synchronises the cluster before the combine).
 template <int F, int S, int NC, int T, bool HALFZ>
 __device__ __forceinline__ void template_columns(int grank, const float* __restrict__ src, int nz,
-                                                 int nfold, const float4* __restrict__ AB) {
+                                                 int nfold, const float4* __restrict__ AB,
+                                                 int s_rt = S) {
   using SM = Smem<F, NC>;
-  constexpr int UPC = ColMap<S, NC>::UPC;
+  constexpr int UPC = S == 1 ? 1 : NC / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if constexpr (F == 4096) {
     // S2: forward passes 1-2; S2-S5 fused: forward pass 3, the product
     // Y = conj(Z) A + Z' B with sum |Y|^2, inverse pass 1; S5: passes 2-3
-    fwd_first_pass<F, S, NC, T, HALFZ>(grank, src, nz, nfold);
+    fwd_first_pass<F, S, NC, T, HALFZ>(grank, src, nz, nfold, s_rt);
     stockham_pass<F, NC, T, 16, 16, false>(SM::cols(), SM::tw2());
-    fused_mid<S, NC, T>(grank, AB, SM::red());
+    fused_mid<S, NC, T>(grank, AB, SM::red(), s_rt);
     if (threadIdx.x == 0) {
       float s = 0.f;
       for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
@@ -646,6 +675,14 @@ __device__ __forceinline__ void template_columns(int grank, const float* __restr
 
 // sigma from the sum |Y|^2 partials of the C CTAs of a group (Eq. PT on the
 // packed spectrum: sigma^2 = 2 sum |Y|^2 / N^2).
+// The same with the group's CTA count C given at run time.
+__device__ __forceinline__ float group_sigma_rt(float* sigpart, int gbase, int C, int N) {
+  cg::cluster_group cluster = cg::this_cluster();
+  float tot = 0.f;
+  for (int q = 0; q < C; ++q) tot += *cluster.map_shared_rank(sigpart, (unsigned)(gbase + q));
+  return sqrtf(2.0f * tot) / (float)N;
+}
+
 template <int S, int NC>
 __device__ __forceinline__ float group_sigma(float* sigpart, int gbase, int N) {
   constexpr int C = ColMap<S, NC>::C;
