@@ -139,11 +139,55 @@ def oracle_sample(seconds: float, max_templates: int, batch: int = 8):
     return done, dt
 
 
+def _oracle_worker(args):
+    """One process of the all-cores baseline: the oracle on its own slice of
+    the bank for about ``seconds``."""
+    first, seconds, batch = args
+    import oracle as O
+    seg, params = S.paper_case()
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        k = first + done
+        bank = O.chirp_bank(params[k:k + batch], 4096.0, 4096, 0.05)
+        O.search(seg.y, bank, KAPPA, k0=k, batch=batch)
+        done += len(bank)
+    return done, time.perf_counter() - t0
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline(seconds: float = 15.0) -> dict:
-    done, dt = oracle_sample(seconds, 4096)
-    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 oracle (own radix-2 FFT, numpy, one process) on the first {done} "
-                       f"templates of the 2^20 bank against the N=2^16 segment, {dt:.1f} s")}
+    """The oracle as it stands on the host cores: one process, then one
+    process per core on disjoint slices of the bank (spawned: the parent has
+    already used the GPU)."""
+    import multiprocessing as mp
+    done, dt = oracle_sample(seconds / 2, 4096)
+    single = done / dt
+    cores = os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(4096 * i, seconds / 2, 8) for i in range(cores)])
+    total = sum(d for d, _ in res)
+    rate = sum(d / t for d, t in res)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": (f"FP64 oracle (own radix-2 FFT, numpy) against the N=2^16 segment: "
+                       f"{cores} processes, one per core, on disjoint slices of the 2^20 bank "
+                       f"({total} templates, ~{seconds / 2:.0f} s each)"),
+            "single_process": {"value": single, "cores": 1,
+                               "sample": f"the first {done} templates, {dt:.1f} s"}}
 
 
 # ---------------------------------------------------------------------------
