@@ -46,15 +46,31 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return out
 
 
-def build(verbose_ptxas: bool = False, force: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def _up_to_date() -> bool:
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "bege.h"))
-    if not force and os.path.exists(LIB):
-        newest = max(os.path.getmtime(p) for p in srcs + headers)
-        if os.path.getmtime(LIB) >= newest:
+    if not os.path.exists(LIB):
+        return False
+    return os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in srcs + headers)
+
+
+def build(verbose_ptxas: bool = False, force: bool = False) -> str:
+    """Compile libbege.so if any source is newer than it.  Processes that
+    build at the same time (one per rank) serialise on a lock file; the
+    second finds the library up to date."""
+    import fcntl
+    os.makedirs(OBJ, exist_ok=True)
+    if not force and _up_to_date():
+        return LIB
+    with open(os.path.join(OBJ, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and _up_to_date():
             return LIB
+        return _build_locked(verbose_ptxas)
+
+
+def _build_locked(verbose_ptxas: bool) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
     tmp = LIB + ".tmp"
