@@ -94,10 +94,13 @@ __device__ __forceinline__ float pow2_scale(float m) {
 }
 
 // G groups of 8 warps per CTA, group g = the CTA's unit g (column slots 2g,
-// 2g + 1); clusters of S / (2 G) CTAs hold the S columns of a template.
+// 2g + 1); clusters of S / (2 G) CTAs hold the S columns of a template.  For
+// S = 2 a template is one unit: the two groups of a CTA then take different
+// templates (k0 + 2c + g, ...) and never wait for each other.
 template <int S, int P, int G>
 __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, CorrelateArgs a) {
-  constexpr int NC = 2 * G;
+  constexpr bool kInd = (S == 2 && G == 2);  // independent groups
+  constexpr int NC = kInd ? 2 : 2 * G;       // columns per CTA in the column map
   constexpr int T = kGT * G;
   using SM = Smem<P, G>;
   using L = TcLay<P, G>;
@@ -131,7 +134,14 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
     else
       SM::tin_b()[c * 64 + x] = root(64 * b * x, H);
   }
-  if (tid < S) {
+  if constexpr (kInd) {
+    if (tid < 2 * S) {  // group gg's columns, in its own region
+      const int gg = tid / S, b = tid % S;
+      int owner, slot;
+      CM::home(b, &owner, &slot);
+      SM::colptr()[S * gg + b] = SM::col(2 * gg + slot);
+    }
+  } else if (tid < S) {
     int owner, slot;
     CM::home(tid, &owner, &slot);
     SM::colptr()[tid] = cluster.map_shared_rank(SM::col(0), (unsigned)owner) + slot * L::CS;
@@ -175,9 +185,12 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
   // this thread's accumulator row (TMEM lane), half of the outputs, slot
   const int trow = 32 * (warp & 3) + lane, th = (warp >> 2) & 1;
   const int tslot_ = 2 * g + (trow >> 6), tr = trow & 63;
-  const int ug = rank * CM::UPC + g;  // the group's unit
+  const int ttab = kInd ? (trow >> 6) : tslot_;  // its column's twiddle-table slot
+  const int ug = kInd ? 0 : rank * CM::UPC + g;  // the group's unit
+  const int64_t kfirst = kInd ? a.k0 + 2 * cid + g : a.k0 + cid;
+  const int kstride = kInd ? 2 * ncl : ncl;
 
-  for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
+  for (int64_t k = kfirst; k < a.k1; k += kstride) {
     // ---- forward GEMM 1 operand: u_c[m1 + 64 m2] = wH^(b m) z[m], K-major;
     // the twiddles of a run of 8 m2 from one product and the step wH^(64 b)
     const float2* z = reinterpret_cast<const float2*>(a.bank + k * a.Lp);
@@ -188,7 +201,7 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int u = lt + i * kGT;
-      const int m1 = u & 63, blk = (u >> 6) & 3, sl = 2 * g + (u >> 8);
+      const int m1 = u & 63, blk = (u >> 6) & 3, sl = kInd ? (u >> 8) : 2 * g + (u >> 8);
       float2 zv[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
@@ -357,8 +370,8 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
     twiddle_to_mn<P, G>(tmem, a_hi, a_lo);
     ok &= gemm<P>(g, lt, tmem, ah, al, bh, bl, true, 128, mbar, parity);
     {  // T_b[n1] = wH^(-b n1) conj(D), n1 = n1a + 64 n1b, to the staging columns
-      const float2 ta = SM::tin_a()[tslot_ * 64 + tr];
-      const float2 step = SM::tin_b()[tslot_ * 64 + 1];
+      const float2 ta = SM::tin_a()[ttab * 64 + tr];
+      const float2 step = SM::tin_b()[ttab * 64 + 1];
       float2* col = SM::col(tslot_);
       const float inv = 1.0f / sy;
 #pragma unroll
@@ -368,7 +381,7 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
 #pragma unroll
         for (int hb = 0; hb < 2; ++hb) {
           const int n1b0 = 32 * th + 16 * q + 8 * hb;
-          float2 tw = cmul(ta, SM::tin_b()[tslot_ * 64 + n1b0]);
+          float2 tw = cmul(ta, SM::tin_b()[ttab * 64 + n1b0]);
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int i = 8 * hb + e;
@@ -380,19 +393,29 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
       }
     }
 
-    cluster.sync();  // every column and sigma partial of the cluster is ready
-    float tot = 0.f;
-#pragma unroll
-    for (int q = 0; q < C; ++q) {
-      const float* sp = cluster.map_shared_rank(SM::sigpart(), (unsigned)q);
-#pragma unroll
-      for (int gg = 0; gg < G; ++gg) tot += sp[gg];
-    }
-    const float sigma = sqrtf(2.0f * tot) / (float)N;
     const int64_t krow = k - a.k0;
-    if (rank == 0 && tid == 0) a.sigma[krow] = sigma;
-    combine_and_emit<kF, S, NC, T>(SM::colptr(), H, rank, a.kappa * sigma, (uint32_t)k, krow, out);
-    cluster.sync();  // remote reads done before the regions are overwritten
+    if constexpr (kInd) {
+      group_sync(g);  // the group's columns and sigma partial are ready
+      const float sigma = sqrtf(2.0f * SM::sigpart()[g]) / (float)N;
+      if (lt == 0) a.sigma[krow] = sigma;
+      combine_and_emit<kF, S, NC, kGT>(SM::colptr() + S * g, H, 0, a.kappa * sigma, (uint32_t)k,
+                                       krow, out, lt);
+      group_sync(g);  // reads done before the region is overwritten
+    } else {
+      cluster.sync();  // every column and sigma partial of the cluster is ready
+      float tot = 0.f;
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        const float* sp = cluster.map_shared_rank(SM::sigpart(), (unsigned)q);
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) tot += sp[gg];
+      }
+      const float sigma = sqrtf(2.0f * tot) / (float)N;
+      if (rank == 0 && tid == 0) a.sigma[krow] = sigma;
+      combine_and_emit<kF, S, NC, T>(SM::colptr(), H, rank, a.kappa * sigma, (uint32_t)k, krow,
+                                     out);
+      cluster.sync();  // remote reads done before the regions are overwritten
+    }
   }
 
   if (!ok && a.status) atomicOr(a.status, 1u);
@@ -404,7 +427,8 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
 
 template <int S, int P, int G>
 cudaError_t launch_tc_t(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
-  constexpr int C = ColMap<S, 2 * G>::C;
+  constexpr bool kInd = (S == 2 && G == 2);
+  constexpr int C = ColMap<S, kInd ? 2 : 2 * G>::C;
   constexpr size_t smem = TcLay<P, G>::total;
   auto kern = correlate_tc_kernel<S, P, G>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -430,7 +454,7 @@ cudaError_t launch_tc_t(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s
   e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
   if (e != cudaSuccess) return e;
   if (max_clusters < 1) return cudaErrorInvalidConfiguration;
-  int64_t want = a.k1 - a.k0;
+  int64_t want = kInd ? (a.k1 - a.k0 + 1) / 2 : a.k1 - a.k0;
   if (a.max_clusters > 0 && want > a.max_clusters) want = a.max_clusters;
   if (want > max_clusters) want = max_clusters;
   cfg.gridDim = dim3((unsigned)(want * C), 1, 1);
@@ -444,7 +468,7 @@ cudaError_t launch_correlate_tc(const PlanDev& p, const CorrelateArgs& a, int pr
   if (a.k1 <= a.k0) return cudaSuccess;
   const bool bf = precision == 1;
   switch (p.g.S) {
-    case 2: return bf ? tc::launch_tc_t<2, tc::BF16X3, 1>(p, a, s) : tc::launch_tc_t<2, tc::FP16X3, 1>(p, a, s);
+    case 2: return bf ? tc::launch_tc_t<2, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<2, tc::FP16X3, 2>(p, a, s);
     case 4: return bf ? tc::launch_tc_t<4, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<4, tc::FP16X3, 2>(p, a, s);
     case 8: return bf ? tc::launch_tc_t<8, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<8, tc::FP16X3, 2>(p, a, s);
     case 16: return bf ? tc::launch_tc_t<16, tc::BF16X3, 2>(p, a, s) : tc::launch_tc_t<16, tc::FP16X3, 2>(p, a, s);

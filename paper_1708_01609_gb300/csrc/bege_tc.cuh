@@ -28,7 +28,7 @@
 // Shared-memory operands use the no-swizzle canonical layout: core matrices
 // of 8 rows x 16 bytes; K-major for GEMM 1 (rows are the column rows, K the
 // transform input) and MN-major for GEMM 2 (written straight from the rows
-// of the GEMM-1 accumulator, so no transpose pass is needed).  One thread
+// of the GEMM-1 accumulator, so no transpose pass is needed).  One thread per group
 // issues the MMAs; completion is signalled through an mbarrier whose wait is
 // bounded (on give-up the kernel flags `status` and carries on, so every
 // barrier is still reached and tensor memory is freed).
