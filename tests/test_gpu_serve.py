@@ -15,9 +15,11 @@ pytestmark = pytest.mark.gpu
 KAPPA = 4.5
 
 
-@pytest.fixture(scope="module")
-def served():
-    ctx = make_ctx(tail_capacity=1 << 20)
+@pytest.fixture(scope="module", params=[0, 1], ids=["fp32", "bf16x3"])
+def served(request):
+    """A context of the given precision (FP32 path, or the BF16x3 precision
+    form) with a resident bank."""
+    ctx = make_ctx(tail_capacity=1 << 20, precision=request.param)
     params = S.grid_paper(64, 96)                     # 6144 in-band chirps
     bank = ctx.bege_define_bank(params, tau=1.0)
     yield ctx, params, bank
