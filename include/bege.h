@@ -186,7 +186,8 @@ int bege_autotune(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begi
  * one persistent kernel launch captured with the batched segment-spectrum
  * kernel in a CUDA graph (Sec. 3.2: batch mode over blocks of segments and
  * groups of templates).  n must be one of 2^14, 2^15, 2^16, 2^17 and the
- * bank's template length at most 4096 samples (tau <= 1 s at 4096 Hz). */
+ * bank's template length at most 4096 samples (tau <= 1 s at 4096 Hz).
+ * Batches always run the FP32 path, whatever the context's precision. */
 typedef struct {
   const float* strain;   /* HOST pointer to n FP32 samples (copied at creation) */
   int64_t n;
