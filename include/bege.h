@@ -233,8 +233,9 @@ int bege_batch_get_plan(bege_ctx* ctx, int32_t batch_id, int32_t* plan, int64_t*
 
 /* Autotuner of the batching form: times every plan (plan 0 over chunks of
  * 64..2048 templates and both orders, plan 1 with the current per-length
- * shapes) with `reps` runs each after one warm-up, keeps the fastest and
- * reports its median time in *best_ms.  Synchronous on `stream`. */
+ * shapes) with `reps` runs each after one warm-up, keeps the fastest (the
+ * per-segment plan only if more than 1% faster than the best persistent one)
+ * and reports its median time in *best_ms.  Synchronous on `stream`. */
 int bege_batch_autotune(bege_ctx* ctx, int32_t batch_id, int32_t reps, void* stream,
                         float* best_ms);
 

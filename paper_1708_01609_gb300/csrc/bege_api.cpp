@@ -1193,6 +1193,9 @@ int bege_batch_autotune(bege_ctx* ctx, int32_t batch_id, int32_t reps, void* str
   for (int64_t c : {64, 128, 256, 512, 1024, 2048})
     for (int32_t o : {0, 1}) cands.push_back({0, c, o});
   cands.push_back({1, b->chunk, 0});
+  // the per-segment plan is kept only if it beats the best persistent
+  // candidate by more than 1%: within timing noise the single launch wins
+  constexpr float kMargin = 0.99f;
   float best = 0.f;
   Cand pick = cands[0];
   for (size_t i = 0; i < cands.size(); ++i) {
@@ -1213,7 +1216,8 @@ int bege_batch_autotune(bege_ctx* ctx, int32_t batch_id, int32_t reps, void* str
     }
     std::sort(t.begin(), t.end());
     const float med = t[t.size() / 2];
-    if (i == 0 || med < best) {
+    const bool better = cands[i].plan == 1 ? med < kMargin * best : med < best;
+    if (i == 0 || better) {
       best = med;
       pick = cands[i];
     }
