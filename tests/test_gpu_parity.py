@@ -170,6 +170,31 @@ def test_paper_scale_sampled(ctx):
         ctx.bege_release(h)
 
 
+@pytest.mark.parametrize("lg", [14, 15, 17])
+def test_full_bank_sampled_other_lengths(ctx, lg):
+    """All 2^20 chirps in one correlate call against noise segments of the
+    other supported lengths (4 s, 8 s and the longest, 32 s); the oracle
+    checks sigma and tails of a sample of templates."""
+    _, params = S.paper_case()
+    n = 1 << lg
+    y = S.band_limited_noise(n, 700 + lg)
+    kappa = 5.0
+    seg = ctx.bege_load_segment(y)
+    bid = ctx.bege_define_bank(params, tau=1.0, taper_frac=0.05)
+    job = ctx.bege_correlate(seg, bid, 0, len(params), kappa)
+    recs, total = ctx.bege_fetch_tails(job)
+    assert total == len(recs) and total > 0
+    sg = ctx.bege_get_sigma(job, len(params))
+    sample = sorted({0, len(params) - 1} | set(rng(lg).integers(0, len(params), 14).tolist()))
+    bank = O.chirp_bank(params[sample], 4096.0, 4096, 0.05)
+    rho, sig = oracle_rho(y, bank)
+    assert np.all(np.abs(sg[sample] / sig - 1) <= 1e-6)
+    ref = {k: (rho[i], sig[i]) for i, k in enumerate(sample)}
+    compare_tails(recs, ref, kappa, tmpl_subset=set(sample))
+    for h in (job, bid, seg):
+        ctx.bege_release(h)
+
+
 # ---------------------------------------------------------------------------
 # Edge cases and errors
 # ---------------------------------------------------------------------------
