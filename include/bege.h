@@ -121,11 +121,17 @@ int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_beg
 /* Wait for job `job_id` and copy its tail records to HOST `out` (capacity
  * records).  *n_total receives the true number of tails; *n_written the
  * number copied = min(n_total, capacity, device tail capacity).  Records are
- * in device completion order (not sorted).  Returns BEGE_EOVERFLOW (with the
+ * in device completion order (bege_sort_tails orders them).  Returns BEGE_EOVERFLOW (with the
  * counts filled in) when n_total exceeds what was copied, BEGE_ETIMEDOUT if
  * a bounded wait inside the kernel gave up (the job's results are invalid). */
 int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capacity,
                      int64_t* n_written, int64_t* n_total);
+
+/* Sort n HOST tail records in place by (template, lag), the order in which
+ * Sec. 3.3 gathers tails per template.  Host only (no context, no device);
+ * (template, lag) pairs are unique within one job, so the order is total.
+ * Errors: EINVAL (NULL records with n > 0, n < 0). */
+int bege_sort_tails(bege_tail* recs, int64_t n);
 
 /* Wait for job `job_id` and report the device time in milliseconds of its
  * correlate kernel alone (CUDA events recorded on the job's stream right

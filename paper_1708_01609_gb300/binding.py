@@ -86,6 +86,7 @@ SIGNATURES = {
     "bege_define_bank_samples": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _PI32]),
     "bege_correlate": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
     "bege_fetch_tails": (ctypes.c_int, [_VP, _I32, _VP, _I64, _PI64, _PI64]),
+    "bege_sort_tails": (ctypes.c_int, [_VP, _I64]),
     "bege_query": (ctypes.c_int, [_VP, _I32]),
     "bege_job_kernel_ms": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_float)]),
     "bege_get_sigma": (ctypes.c_int, [_VP, _I32, _VP, _I64]),
@@ -228,11 +229,13 @@ class Context:
                                        ctypes.byref(jid)), "bege_correlate")
         return jid.value
 
-    def bege_fetch_tails(self, job: int, capacity: int | None = None, out: np.ndarray | None = None):
+    def bege_fetch_tails(self, job: int, capacity: int | None = None, out: np.ndarray | None = None,
+                         sort: bool = False):
         """Returns (records as TAIL_DTYPE array, n_total).
 
         With neither ``capacity`` nor ``out`` the true count is queried first
-        and a buffer of that size is used."""
+        and a buffer of that size is used.  ``sort``: records in (template,
+        lag) order (bege_sort_tails) instead of device completion order."""
         nw, nt = _I64(), _I64()
         if out is None:
             if capacity is None:
@@ -244,7 +247,10 @@ class Context:
         _check(self.lib.bege_fetch_tails(self.h, job, _ptr(out), len(out), ctypes.byref(nw),
                                          ctypes.byref(nt)), "bege_fetch_tails",
                ok=(BEGE_OK, BEGE_EOVERFLOW))
-        return out[: nw.value], nt.value
+        recs = out[: nw.value]
+        if sort:
+            bege_sort_tails(recs)
+        return recs, nt.value
 
     def bege_query(self, job: int) -> bool:
         return _check(self.lib.bege_query(self.h, job), "bege_query",
@@ -427,6 +433,15 @@ def bege_search_noalloc(strain_dev: int, n: int, bank_dev: int, ld: int, k_begin
     _check(lib.bege_search_noalloc(strain_dev, n, bank_dev, ld, k_begin, k_end, kappa,
                                    sigma_dev, tails_dev, tail_capacity, tail_count_dev, stream),
            "bege_search_noalloc")
+
+
+def bege_sort_tails(recs: np.ndarray) -> np.ndarray:
+    """Sort TAIL_DTYPE records in place by (template, lag); returns them."""
+    if recs.dtype != TAIL_DTYPE or not recs.flags.c_contiguous:
+        raise ValueError("records must be a contiguous TAIL_DTYPE array")
+    _check(load_library().bege_sort_tails(_ptr(recs) if len(recs) else None, len(recs)),
+           "bege_sort_tails")
+    return recs
 
 
 def bege_version() -> str:

@@ -752,6 +752,14 @@ int bege_query(bege_ctx* ctx, int32_t job_id) {
   return BEGE_OK;
 }
 
+int bege_sort_tails(bege_tail* recs, int64_t n) {
+  if (n < 0 || (n > 0 && !recs)) return fail(BEGE_EINVAL, "bad record array");
+  std::sort(recs, recs + n, [](const bege_tail& x, const bege_tail& y) {
+    return x.tmpl != y.tmpl ? x.tmpl < y.tmpl : x.lag < y.lag;
+  });
+  return BEGE_OK;
+}
+
 int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capacity,
                      int64_t* n_written, int64_t* n_total) {
   if (!ctx || !n_written || !n_total) return fail(BEGE_EINVAL, "NULL argument");

@@ -72,3 +72,23 @@ def test_null_arguments_rejected(lib):
     assert lib.bege_create(None, 0, None) == -1
     assert lib.bege_destroy(None) == -1
     assert lib.bege_release(None, 1) == -1
+
+
+def test_sort_tails_orders_by_template_then_lag():
+    """bege_sort_tails is host-only: records in (template, lag) order, values
+    carried along, the empty array accepted and a bad array rejected."""
+    import numpy as np
+    from paper_1708_01609_gb300 import binding
+    g = np.random.default_rng(3)
+    pairs = np.unique(g.integers(0, 1 << 20, (5000, 2)).astype(np.uint32), axis=0)
+    pairs = pairs[g.permutation(len(pairs))]
+    recs = np.empty(len(pairs), dtype=binding.TAIL_DTYPE)
+    recs["tmpl"], recs["lag"] = pairs[:, 0], pairs[:, 1]
+    recs["value"] = (pairs[:, 0].astype(np.float64) - pairs[:, 1]).astype(np.float32)
+    want = recs[np.lexsort((recs["lag"], recs["tmpl"]))].copy()
+    got = binding.bege_sort_tails(recs)
+    assert np.array_equal(got, want)
+    binding.bege_sort_tails(np.empty(0, dtype=binding.TAIL_DTYPE))
+    lib = binding.load_library()
+    assert lib.bege_sort_tails(None, 5) == binding.BEGE_EINVAL
+    assert lib.bege_sort_tails(None, -1) == binding.BEGE_EINVAL
