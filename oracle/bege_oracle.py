@@ -228,6 +228,47 @@ def search(y: np.ndarray, templates: np.ndarray, kappa: float, k0: int = 0,
     return out
 
 
+# ----------------------------------------------------------------------------
+# Per-lag maximum over the bank (Eq. Ak, Eq. Aa, Eq. BA; Table 3)
+# ----------------------------------------------------------------------------
+def max_projection(rho: np.ndarray, sigma: np.ndarray, kappa: float, k0: int = 0):
+    """The per-lag projection of a bank's correlations onto one array of size
+    N (Eq. Ak over the templates of a bank, gathered as in Eq. Aa and Eq. BA
+    with the maximal value kept per sample): for every lag n, among the
+    templates k whose rho_k[n] > kappa sigma_k, the largest normalised value
+    rho_k[n] / sigma_k and its template (reading: the signed value, as in
+    Eq. C; the strict threshold of Eq. tail; equal values go to the smaller
+    template index).  Returns (snr, tmpl): snr 0 and tmpl -1 where no
+    template passes.  rho: (K, N); sigma: (K,); template index = k0 + row.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    n = rho.shape[1]
+    snr = np.zeros(n)
+    tmpl = np.full(n, -1, dtype=np.int64)
+    for r in range(rho.shape[0]):
+        hit = rho[r] > kappa * sigma[r]
+        val = rho[r] / sigma[r]
+        better = hit & (val > snr)
+        better |= hit & (tmpl < 0)
+        snr[better] = val[better]
+        tmpl[better] = k0 + r
+    return snr, tmpl
+
+
+def table3_rows(snr: np.ndarray, tmpl: np.ndarray, f0: np.ndarray) -> np.ndarray:
+    """Table 3's encoding of a projection: one row per lag with a hit, the
+    sample offset (1-based, as the table counts), 1000 x snr as an integer
+    and the hit template's initial frequency f0 [Hz] as an integer."""
+    lags = np.nonzero(tmpl >= 0)[0]
+    rows = np.empty(len(lags), dtype=[("offset", np.int64), ("rho1000", np.int32),
+                                       ("f0", np.int32)])
+    rows["offset"] = lags + 1
+    rows["rho1000"] = np.floor(1000.0 * snr[lags]).astype(np.int32)
+    rows["f0"] = np.floor(np.asarray(f0)[tmpl[lags]]).astype(np.int32)
+    return rows
+
+
 def near_threshold(values: np.ndarray, sigma: np.ndarray, kappa: float,
                    band: float = 1e-3) -> np.ndarray:
     """True where ||rho| - kappa sigma| <= band * sigma (excluded from set parity)."""

@@ -312,3 +312,65 @@ def test_noise_recipe():
     f = np.arange(n // 2 + 1) * 4096.0 / n
     outside = (f < 350) | (f > 2000)
     assert spec[outside].sum() < 1e-9 * spec.sum()
+
+
+# ----------------------------------------------------------------------------
+# Per-lag maximum over the bank (Eq. Ak, Eq. Aa, Eq. BA) and Table 3
+# ----------------------------------------------------------------------------
+def test_max_projection_matches_brute_force():
+    """Scalar loops over lags and templates, written from the definition:
+    keep the largest rho/sigma among templates with rho > kappa sigma, the
+    smaller template on equal values."""
+    g = np.random.default_rng(41)
+    k, n = 7, 40
+    rho = g.standard_normal((k, n)) * 2.0
+    rho[3, 5] = rho[1, 5] = 9.0                     # an exact tie: template 1 wins
+    sigma = np.ones(k)
+    sigma[4] = 0.5                                  # normalisation matters
+    kappa = 1.5
+    snr, tmpl = O.max_projection(rho, sigma, kappa, k0=100)
+    for j in range(n):
+        best, arg = 0.0, -1
+        for r in range(k):
+            if rho[r, j] > kappa * sigma[r]:
+                v = rho[r, j] / sigma[r]
+                if arg < 0 or v > best:
+                    best, arg = v, 100 + r
+        assert tmpl[j] == arg and snr[j] == best
+    assert tmpl[5] == 101
+    # negative correlations are not hits of the projection (signed, Eq. C)
+    neg = -np.abs(rho)
+    assert np.all(O.max_projection(neg, sigma, kappa)[1] == -1)
+
+
+def test_max_projection_is_the_per_lag_maximum_of_the_tails():
+    """The projection keeps, per lag, the largest positive tail of the
+    all-hits search, normalised by its template's sigma."""
+    y = S.band_limited_noise(1024, 12)
+    bank = S.random_samples_bank(9, 200, 13).astype(np.float64)
+    kappa = 2.0
+    res = O.search(y, bank, kappa, return_rho=True)
+    snr, tmpl = O.max_projection(res["rho"], res["sigma"], kappa)
+    t = res["tails"]
+    t = t[t["value"] > 0]
+    for j in range(1024):
+        at = t[t["lag"] == j]
+        if len(at) == 0:
+            assert tmpl[j] == -1 and snr[j] == 0.0
+            continue
+        norm = at["value"] / res["sigma"][at["tmpl"]]
+        i = int(np.argmax(norm))
+        assert tmpl[j] == at["tmpl"][i] and snr[j] == norm[i]
+
+
+def test_table3_rows_encoding():
+    """Table 3: 1-based sample offset, 1000 rho as a 4-byte integer, the
+    template's initial frequency in whole Hz; lags without a hit are left out."""
+    snr = np.array([0.0, 5.5227, 0.0, 6.0])
+    tmpl = np.array([-1, 2, -1, 0])
+    f0 = np.array([486.7, 500.0, 623.2])
+    rows = O.table3_rows(snr, tmpl, f0)
+    assert rows["offset"].tolist() == [2, 4]
+    assert rows["rho1000"].tolist() == [5522, 6000]
+    assert rows["f0"].tolist() == [623, 486]
+    assert rows["rho1000"].dtype == np.int32
