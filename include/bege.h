@@ -127,6 +127,26 @@ int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_beg
 int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capacity,
                      int64_t* n_written, int64_t* n_total);
 
+/* As bege_correlate, and the job also projects its hits onto one array of
+ * the segment's N lags, keeping per lag the largest normalised value over
+ * the bank (Eq. Ak over the templates, gathered as in Eq. Aa / Eq. BA with
+ * the maximal value kept per sample): among templates k with
+ * rho_k[n] > kappa sigma_k (signed, as Eq. C; strict, as Eq. tail), the
+ * largest rho_k[n] / sigma_k and its template.  Raised with a 64-bit atomic
+ * maximum on (value bits, complemented template), so equal values keep the
+ * smaller template and the result does not depend on timing (the paper's
+ * post-callback race, Sec. 3.3, does not arise).  All-hit records are still
+ * collected as for bege_correlate.  Extra device memory: 8 N bytes.
+ * Errors: as bege_correlate. */
+int bege_correlate_max(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                       int64_t k_end, float kappa, void* stream, int32_t* job_id);
+
+/* Wait for a bege_correlate_max job and copy its projection to HOST arrays
+ * of n = N entries: snr[n] = rho / sigma of the kept hit and tmpl[n] its
+ * template index, or snr 0 and tmpl -1 where no template passes.
+ * Errors: EINVAL (not such a job, n != N), ETIMEDOUT, ECUDA. */
+int bege_fetch_max(bege_ctx* ctx, int32_t job_id, float* snr, int32_t* tmpl, int64_t n);
+
 /* Sort n HOST tail records in place by (template, lag), the order in which
  * Sec. 3.3 gathers tails per template.  Host only (no context, no device);
  * (template, lag) pairs are unique within one job, so the order is total.

@@ -85,6 +85,8 @@ SIGNATURES = {
                                         _PI32]),
     "bege_define_bank_samples": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _PI32]),
     "bege_correlate": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
+    "bege_correlate_max": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
+    "bege_fetch_max": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64]),
     "bege_fetch_tails": (ctypes.c_int, [_VP, _I32, _VP, _I64, _PI64, _PI64]),
     "bege_sort_tails": (ctypes.c_int, [_VP, _I64]),
     "bege_query": (ctypes.c_int, [_VP, _I32]),
@@ -228,6 +230,20 @@ class Context:
         _check(self.lib.bege_correlate(self.h, seg, bank, k_begin, k_end, kappa, stream,
                                        ctypes.byref(jid)), "bege_correlate")
         return jid.value
+
+    def bege_correlate_max(self, seg: int, bank: int, k_begin: int, k_end: int, kappa: float,
+                           stream: int = 0) -> int:
+        jid = _I32()
+        _check(self.lib.bege_correlate_max(self.h, seg, bank, k_begin, k_end, kappa, stream,
+                                           ctypes.byref(jid)), "bege_correlate_max")
+        return jid.value
+
+    def bege_fetch_max(self, job: int, n: int):
+        """Returns (snr FP32 array, template int32 array) of n = N lags."""
+        snr = np.empty(n, dtype=np.float32)
+        tmpl = np.empty(n, dtype=np.int32)
+        _check(self.lib.bege_fetch_max(self.h, job, _ptr(snr), _ptr(tmpl), n), "bege_fetch_max")
+        return snr, tmpl
 
     def bege_fetch_tails(self, job: int, capacity: int | None = None, out: np.ndarray | None = None,
                          sort: bool = False):

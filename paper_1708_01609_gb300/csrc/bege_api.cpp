@@ -85,6 +85,8 @@ struct Job {
   int64_t k0 = 0, k1 = 0;
   float kappa = 0.f;
   std::unique_ptr<JobBuffers> buf;
+  DevBuf proj;        // per-lag maximum over the bank (bege_correlate_max), n_proj words
+  int64_t n_proj = 0;
   cudaEvent_t done = nullptr;
   cudaEvent_t k_start = nullptr, k_stop = nullptr;  // around the correlate kernel
 };
@@ -513,6 +515,7 @@ int bege_destroy(bege_ctx* ctx) {
     for (auto& kv : ctx->jobs) {
       if (kv.second->done) cudaEventSynchronize(kv.second->done);
       destroy_job_events(kv.second.get());
+      ctx->release(&kv.second->proj);
       ctx->release(&kv.second->buf->sigma);
       ctx->release(&kv.second->buf->recs);
       ctx->release(&kv.second->buf->counter);
@@ -651,7 +654,7 @@ int bege_define_bank_samples(bege_ctx* ctx, const float* samples, int64_t count,
 
 static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
                           int64_t k_end, float kappa, cudaStream_t s, float* dump_dev,
-                          int32_t* job_id) {
+                          int32_t* job_id, bool project = false) {
   auto si = ctx->segs.find(seg_id);
   if (si == ctx->segs.end()) return fail(BEGE_EINVAL, "unknown segment handle");
   auto bi = ctx->banks.find(bank_id);
@@ -677,7 +680,16 @@ static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
   job->kappa = kappa;
   int rc = take_job_buffers(ctx, nsig, ctx->cfg.tail_capacity, &job->buf);
   if (rc) return rc;
+  if (project) {
+    rc = ctx->alloc(&job->proj, (size_t)seg->n * sizeof(unsigned long long));
+    if (rc) {
+      ctx->pool.push_back(std::move(job->buf));
+      return rc;
+    }
+    job->n_proj = seg->n;
+  }
   cudaError_t e = cudaEventCreateWithFlags(&job->done, cudaEventDisableTiming);
+  if (e == cudaSuccess && project) e = cudaMemsetAsync(job->proj.ptr, 0, job->proj.bytes, s);
   if (e == cudaSuccess) e = cudaEventCreate(&job->k_start);
   if (e == cudaSuccess) e = cudaEventCreate(&job->k_stop);
   if (e == cudaSuccess) e = cudaMemsetAsync(job->buf->counter.ptr, 0, 16, s);
@@ -697,6 +709,7 @@ static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
     a.dump = dump_dev;
     a.max_clusters = 0;
     a.status = reinterpret_cast<unsigned int*>(static_cast<char*>(job->buf->counter.ptr) + 8);
+    a.proj = static_cast<unsigned long long*>(job->proj.ptr);
     if (ctx->cfg.precision != 0) {
       e = bege::launch_correlate_tc(seg->plan->dev, a, ctx->cfg.precision, s);
     } else {
@@ -710,6 +723,7 @@ static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
   if (e == cudaSuccess) e = cudaEventRecord(job->done, s);
   if (e != cudaSuccess) {
     destroy_job_events(job.get());
+    ctx->release(&job->proj);
     ctx->pool.push_back(std::move(job->buf));
     return cuda_fail(e, "correlate");
   }
@@ -726,6 +740,49 @@ int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_beg
   std::lock_guard<std::mutex> lk(ctx->mu);
   return correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, kappa,
                         static_cast<cudaStream_t>(stream), nullptr, job_id);
+}
+
+int bege_correlate_max(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                       int64_t k_end, float kappa, void* stream, int32_t* job_id) {
+  if (!ctx || !job_id) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, kappa,
+                        static_cast<cudaStream_t>(stream), nullptr, job_id, true);
+}
+
+int bege_fetch_max(bege_ctx* ctx, int32_t job_id, float* snr, int32_t* tmpl, int64_t n) {
+  if (!ctx || !snr || !tmpl) return fail(BEGE_EINVAL, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Job* j = find_job(ctx, job_id);
+  if (!j) return fail(BEGE_EINVAL, "unknown job handle");
+  if (!j->proj.ptr) return fail(BEGE_EINVAL, "the job was not started by bege_correlate_max");
+  if (n != j->n_proj) return fail(BEGE_EINVAL, "n must equal the segment length");
+  cudaError_t e = cudaEventSynchronize(j->done);
+  if (e != cudaSuccess) return cuda_fail(e, "job");
+  unsigned long long cs[2] = {0, 0};
+  e = cudaMemcpy(cs, j->buf->counter.ptr, 16, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "tail count");
+  if (cs[1] & 0xffffffffull)
+    return fail(BEGE_ETIMEDOUT, "a bounded device wait gave up; results of this job are invalid");
+  std::vector<unsigned long long> w((size_t)n);
+  e = cudaMemcpy(w.data(), j->proj.ptr, (size_t)n * sizeof(unsigned long long),
+                 cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "projection");
+  for (int64_t i = 0; i < n; ++i) {
+    if (w[i] == 0) {
+      snr[i] = 0.f;
+      tmpl[i] = -1;
+    } else {
+      const uint32_t hi = (uint32_t)(w[i] >> 32);
+      float v;
+      std::memcpy(&v, &hi, sizeof v);
+      snr[i] = v;
+      tmpl[i] = (int32_t)(~(uint32_t)(w[i] & 0xffffffffull));
+    }
+  }
+  return BEGE_OK;
 }
 
 int bege_job_kernel_ms(bege_ctx* ctx, int32_t job_id, float* ms) {
@@ -1245,6 +1302,7 @@ int bege_release(bege_ctx* ctx, int32_t handle) {
   if (ji != ctx->jobs.end()) {
     cudaEventSynchronize(ji->second->done);
     destroy_job_events(ji->second.get());
+    ctx->release(&ji->second->proj);
     ctx->pool.push_back(std::move(ji->second->buf));
     ctx->jobs.erase(ji);
     return BEGE_OK;

@@ -64,10 +64,10 @@ __device__ __forceinline__ void run_item(const BatchArgs& b, const ItemState* st
       const float thr = st->sg.kappa * sigma;
       float2* const* cp = Smem<kF, kNC>::colptr();
       switch (S) {
-        case 2: combine_and_emit<kF, 2, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out); break;
-        case 4: combine_and_emit<kF, 4, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out); break;
-        case 8: combine_and_emit<kF, 8, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out); break;
-        default: combine_and_emit<kF, 16, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out); break;
+        case 2: combine_and_emit<kF, 2, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out, 0.f); break;
+        case 4: combine_and_emit<kF, 4, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out, 0.f); break;
+        case 8: combine_and_emit<kF, 8, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out, 0.f); break;
+        default: combine_and_emit<kF, 16, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out, 0.f); break;
       }
     }
     if (C == 1) __syncthreads(); else cluster.sync();

@@ -539,12 +539,15 @@ struct TailOut {
   uint64_t cap;
   unsigned long long* counter;
   float* dump;
+  // optional per-lag maximum over the bank (Eq. Ak): one 64-bit word per
+  // lag, (bits of rho/sigma) << 32 | ~template, raised with atomicMax
+  unsigned long long* proj = nullptr;
 };
 
 template <int F, int S, int NC, int T>
 __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, int rank, float thr,
                                                  uint32_t tmpl, int64_t krow, const TailOut& a,
-                                                 int tix = threadIdx.x) {
+                                                 float inv_sigma, int tix = threadIdx.x) {
   constexpr int C = ColMap<S, NC>::C;
   constexpr int per = F / C;
   static_assert(per % T == 0, "combine rounds");
@@ -593,13 +596,21 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           if ((mask >> (2 * n2 + e)) & 1u) {
+            const uint32_t lag = (uint32_t)(2 * (n1 + F * n2) + e);
+            const float v = (e ? t[n2].y : t[n2].x) * invH;
             if (pos < a.cap) {
               bege_tail* r = a.recs + pos;
               r->tmpl = tmpl;
-              r->lag = (uint32_t)(2 * (n1 + F * n2) + e);
-              r->value = (e ? t[n2].y : t[n2].x) * invH;
+              r->lag = lag;
+              r->value = v;
             }
             ++pos;
+            // positive values above the threshold: v > thr > 0, so the bits
+            // of v / sigma order like the values; equal values keep the
+            // smaller template (larger ~tmpl)
+            if (a.proj && v > thr)
+              atomicMax(a.proj + lag, ((unsigned long long)__float_as_uint(v * inv_sigma) << 32) |
+                                          (unsigned long long)(~tmpl));
           }
         }
       }
@@ -708,7 +719,7 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
   const int ncl = gridDim.x / C;
   const int nz = (int)(a.Lp / 2);
   const int nfold = (nz + F - 1) / F;
-  const TailOut out{a.recs, a.cap, a.counter, a.dump};
+  const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj};
 
   for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
     template_columns<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold, a.AB);
@@ -718,7 +729,7 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
     if (rank == 0 && threadIdx.x == 0) a.sigma[krow] = sigma;
     // S6: S-point combine, threshold, warp-ballot compaction
     combine_and_emit<F, S, NC, T>(Smem<F, NC>::colptr(), H, rank, a.kappa * sigma, (uint32_t)k,
-                                  krow, out);
+                                  krow, out, 1.0f / sigma);
     cluster.sync();  // remote reads done before the columns are overwritten
   }
 }

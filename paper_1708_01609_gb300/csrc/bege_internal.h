@@ -91,6 +91,7 @@ struct CorrelateArgs {
   float* dump;
   int max_clusters;      // 0 = as many as fit
   unsigned int* status;  // optional: set non-zero by a kernel whose bounded wait gave up
+  unsigned long long* proj = nullptr;  // optional: per-lag maximum over the bank (Eq. Ak)
 };
 cudaError_t launch_correlate(const PlanDev& p, const CorrelateArgs& a, CorrConfig cfg,
                              cudaStream_t s);

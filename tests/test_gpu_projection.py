@@ -1,0 +1,114 @@
+"""Per-lag maximum over the bank (Eq. Ak, Aa, BA) on the GPU: against the
+oracle's projection, against the per-lag maximum of the job's own all-hit
+records (bitwise: same FP32 values), and in Table 3's encoding."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from gpu_helpers import make_ctx, oracle_rho
+
+pytestmark = pytest.mark.gpu
+
+
+def projection_of_records(recs, sigma, kappa, n, k0=0):
+    """The kernel's rule on its own records: v > fl(kappa sigma), key
+    fl(v (1 / sigma)), ties to the smaller template; in FP32."""
+    sig = sigma.astype(np.float32)
+    k = recs["tmpl"].astype(np.int64) - k0
+    v = recs["value"].astype(np.float32)
+    thr = np.float32(kappa) * sig[k]
+    sel = v > thr
+    v, k, lag = v[sel], k[sel], recs["lag"][sel].astype(np.int64)
+    snr = v * (np.float32(1.0) / sig[k])
+    order = np.lexsort((k, -snr.astype(np.float64), lag))   # per lag: largest snr, then smallest k
+    lag, snr, k = lag[order], snr[order], k[order]
+    first = np.ones(len(lag), bool)
+    first[1:] = lag[1:] != lag[:-1]
+    out_snr = np.zeros(n, np.float32)
+    out_k = np.full(n, -1, np.int32)
+    out_snr[lag[first]] = snr[first]
+    out_k[lag[first]] = (k[first] + k0).astype(np.int32)
+    return out_snr, out_k
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_projection_matches_oracle(prec):
+    seg_data, params = S.small_case()
+    kappa = 4.0
+    ctx = make_ctx(tail_capacity=1 << 20, precision=prec)
+    seg = ctx.bege_load_segment(seg_data.y)
+    bid = ctx.bege_define_bank(params)
+    job = ctx.bege_correlate_max(seg, bid, 0, len(params), kappa)
+    snr, tmpl = ctx.bege_fetch_max(job, len(seg_data.y))
+    ctx.close()
+    bank = O.chirp_bank(params, 4096.0, 4096, 0.05)
+    rho, sig = oracle_rho(seg_data.y, bank)
+    o_snr, o_tmpl = O.max_projection(rho, sig, kappa)
+    tol = 1e-5 if prec == 0 else 2e-3
+    both = (tmpl >= 0) & (o_tmpl >= 0)
+    assert both.sum() > 100
+    at_gpu_pick = rho[tmpl[both], np.flatnonzero(both)] / sig[tmpl[both]]
+    assert np.all(np.abs(snr[both] - at_gpu_pick) <= tol)          # value of the kept hit
+    assert np.all(at_gpu_pick >= o_snr[both] - 2 * tol)            # it is a maximum
+    only = (tmpl >= 0) != (o_tmpl >= 0)
+    # a lag with a hit on one side only has its best value at the threshold
+    best = np.where(o_tmpl >= 0, o_snr, (rho / sig[:, None]).max(axis=0))
+    assert np.all(np.abs(best[only] - kappa) <= max(1e-3, 2 * tol))
+    k_inj, lag, _ = seg_data.injections[0]
+    assert tmpl[lag] >= 0 and snr[lag] >= rho[k_inj, lag] / sig[k_inj] - tol
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_projection_is_the_maximum_of_the_records(prec):
+    """65536 chirps of the paper bank at N = 2^16 with its injections (many
+    templates hit the same lags): the projection equals, bitwise, the per-lag
+    maximum recomputed from the job's own records and sigma."""
+    seg_data, params = S.paper_case(seed=2017)
+    kappa, nt, n = 5.5, 65536, len(seg_data.y)
+    ctx = make_ctx(tail_capacity=1 << 24, precision=prec)
+    seg = ctx.bege_load_segment(seg_data.y)
+    bid = ctx.bege_define_bank(params[:nt], tau=1.0, taper_frac=0.05)
+    job = ctx.bege_correlate_max(seg, bid, 0, nt, kappa)
+    snr, tmpl = ctx.bege_fetch_max(job, n)
+    recs, total = ctx.bege_fetch_tails(job)
+    sigma = ctx.bege_get_sigma(job, nt)
+    ctx.close()
+    assert total == len(recs) > 1000
+    r_snr, r_tmpl = projection_of_records(recs, sigma, kappa, n)
+    assert np.array_equal(tmpl, r_tmpl)
+    assert np.array_equal(snr.view(np.uint32), r_snr.view(np.uint32))
+    assert (tmpl >= 0).sum() > 100
+
+
+def test_table3_encoding_of_a_gpu_projection():
+    from paper_1708_01609_gb300.output import table3_rows
+    seg_data, params = S.small_case()
+    ctx = make_ctx(tail_capacity=1 << 20)
+    seg = ctx.bege_load_segment(seg_data.y)
+    bid = ctx.bege_define_bank(params)
+    job = ctx.bege_correlate_max(seg, bid, 0, len(params), 4.0)
+    snr, tmpl = ctx.bege_fetch_max(job, len(seg_data.y))
+    ctx.close()
+    rows = table3_rows(snr, tmpl, params[:, 0])
+    ref = O.table3_rows(snr.astype(np.float64), tmpl.astype(np.int64), params[:, 0])
+    assert len(rows) == len(ref) > 0
+    assert np.array_equal(rows["offset"], ref["offset"])
+    assert np.array_equal(rows["rho1000"], ref["rho1000"])
+    assert np.array_equal(rows["f0"], ref["f0"])
+    assert rows["rho1000"].min() >= 4000
+
+
+def test_fetch_max_rejects_plain_jobs_and_wrong_length():
+    from paper_1708_01609_gb300.binding import BegeError
+    seg_data, params = S.small_case()
+    ctx = make_ctx(tail_capacity=1 << 20)
+    seg = ctx.bege_load_segment(seg_data.y)
+    bid = ctx.bege_define_bank(params)
+    plain = ctx.bege_correlate(seg, bid, 0, len(params), 4.0)
+    with pytest.raises(BegeError):
+        ctx.bege_fetch_max(plain, len(seg_data.y))
+    job = ctx.bege_correlate_max(seg, bid, 0, len(params), 4.0)
+    with pytest.raises(BegeError):
+        ctx.bege_fetch_max(job, len(seg_data.y) // 2)
+    ctx.close()
