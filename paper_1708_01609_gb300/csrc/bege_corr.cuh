@@ -544,7 +544,9 @@ struct TailOut {
   unsigned long long* proj = nullptr;
 };
 
-template <int F, int S, int NC, int T>
+// PROJ: also raise the per-lag maximum a.proj (compiled only into the kernels
+// that serve bege_correlate_max, so the others keep their code unchanged).
+template <int F, int S, int NC, int T, bool PROJ = false>
 __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, int rank, float thr,
                                                  uint32_t tmpl, int64_t krow, const TailOut& a,
                                                  float inv_sigma, int tix = threadIdx.x) {
@@ -596,21 +598,23 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           if ((mask >> (2 * n2 + e)) & 1u) {
-            const uint32_t lag = (uint32_t)(2 * (n1 + F * n2) + e);
-            const float v = (e ? t[n2].y : t[n2].x) * invH;
             if (pos < a.cap) {
               bege_tail* r = a.recs + pos;
               r->tmpl = tmpl;
-              r->lag = lag;
-              r->value = v;
+              r->lag = (uint32_t)(2 * (n1 + F * n2) + e);
+              r->value = (e ? t[n2].y : t[n2].x) * invH;
             }
             ++pos;
-            // positive values above the threshold: v > thr > 0, so the bits
-            // of v / sigma order like the values; equal values keep the
-            // smaller template (larger ~tmpl)
-            if (a.proj && v > thr)
-              atomicMax(a.proj + lag, ((unsigned long long)__float_as_uint(v * inv_sigma) << 32) |
-                                          (unsigned long long)(~tmpl));
+            if constexpr (PROJ) {
+              // positive values above the threshold: v > thr > 0, so the
+              // bits of v / sigma order like the values; equal values keep
+              // the smaller template (larger ~tmpl)
+              const float v = (e ? t[n2].y : t[n2].x) * invH;
+              if (a.proj && v > thr)
+                atomicMax(a.proj + (2 * (n1 + F * n2) + e),
+                          ((unsigned long long)__float_as_uint(v * inv_sigma) << 32) |
+                              (unsigned long long)(~tmpl));
+            }
           }
         }
       }
@@ -705,7 +709,7 @@ __device__ __forceinline__ float group_sigma(float* sigpart, int gbase, int N) {
   return sqrtf(2.0f * tot) / (float)N;
 }
 
-template <int F, int S, int NC, int T, int MINB, bool HALFZ>
+template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool PROJ>
 __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, CorrelateArgs a) {
   constexpr int C = ColMap<S, NC>::C;
   cg::cluster_group cluster = cg::this_cluster();
@@ -728,8 +732,8 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
     const int64_t krow = k - a.k0;
     if (rank == 0 && threadIdx.x == 0) a.sigma[krow] = sigma;
     // S6: S-point combine, threshold, warp-ballot compaction
-    combine_and_emit<F, S, NC, T>(Smem<F, NC>::colptr(), H, rank, a.kappa * sigma, (uint32_t)k,
-                                  krow, out, 1.0f / sigma);
+    combine_and_emit<F, S, NC, T, PROJ>(Smem<F, NC>::colptr(), H, rank, a.kappa * sigma,
+                                        (uint32_t)k, krow, out, PROJ ? 1.0f / sigma : 0.f);
     cluster.sync();  // remote reads done before the columns are overwritten
   }
 }
@@ -742,11 +746,11 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int F, int S, int NC, int T, int MINB, bool HALFZ>
-static cudaError_t launch_corr_t(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
+template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool PROJ>
+static cudaError_t launch_corr_tp(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
   constexpr int C = ColMap<S, NC>::C;
   constexpr size_t smem = Lay<F, NC>::total;
-  auto kern = correlate_kernel<F, S, NC, T, MINB, HALFZ>;
+  auto kern = correlate_kernel<F, S, NC, T, MINB, HALFZ, PROJ>;
   cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -775,6 +779,13 @@ static cudaError_t launch_corr_t(const PlanDev& p, const CorrelateArgs& a, cudaS
   if (want > max_clusters) want = max_clusters;
   cfg.gridDim = dim3((unsigned)(want * C), 1, 1);
   return cudaLaunchKernelEx(&cfg, kern, p, a);
+}
+
+// The projection epilogue (bege_correlate_max) runs in its own instantiation.
+template <int F, int S, int NC, int T, int MINB, bool HALFZ>
+static cudaError_t launch_corr_t(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
+  return a.proj ? launch_corr_tp<F, S, NC, T, MINB, HALFZ, true>(p, a, s)
+                : launch_corr_tp<F, S, NC, T, MINB, HALFZ, false>(p, a, s);
 }
 
 template <int F, int S, int NC, int T>

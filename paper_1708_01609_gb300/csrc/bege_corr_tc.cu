@@ -398,8 +398,8 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
       group_sync(g);  // the group's columns and sigma partial are ready
       const float sigma = sqrtf(2.0f * SM::sigpart()[g]) / (float)N;
       if (lt == 0) a.sigma[krow] = sigma;
-      combine_and_emit<kF, S, NC, kGT>(SM::colptr() + S * g, H, 0, a.kappa * sigma, (uint32_t)k,
-                                       krow, out, 1.0f / sigma, lt);
+      combine_and_emit<kF, S, NC, kGT, true>(SM::colptr() + S * g, H, 0, a.kappa * sigma,
+                                             (uint32_t)k, krow, out, 1.0f / sigma, lt);
       group_sync(g);  // reads done before the region is overwritten
     } else {
       cluster.sync();  // every column and sigma partial of the cluster is ready
@@ -412,8 +412,8 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
       }
       const float sigma = sqrtf(2.0f * tot) / (float)N;
       if (rank == 0 && tid == 0) a.sigma[krow] = sigma;
-      combine_and_emit<kF, S, NC, T>(SM::colptr(), H, rank, a.kappa * sigma, (uint32_t)k, krow,
-                                     out, 1.0f / sigma);
+      combine_and_emit<kF, S, NC, T, true>(SM::colptr(), H, rank, a.kappa * sigma, (uint32_t)k,
+                                           krow, out, 1.0f / sigma);
       cluster.sync();  // remote reads done before the regions are overwritten
     }
   }
