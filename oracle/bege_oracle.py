@@ -100,16 +100,27 @@ def taper(length: int, frac: float) -> np.ndarray:
 
 
 def chirp_template(f0: float, fdot: float, fs: float, length: int,
-                   taper_frac: float) -> np.ndarray:
-    """Unit-norm tapered linear chirp, FP64, length ``length``."""
+                   taper_frac: float, symmetric: bool = False) -> np.ndarray:
+    """Unit-norm tapered linear chirp, FP64, length ``length``.
+
+    symmetric: the time-symmetric chirp of the paper's banks (Fig. 2
+    caption: the superposition of the chirp forward and backward in time),
+    read on the sample grid as sin(phi(m)) + sin(phi(L - 1 - m)) under the
+    (symmetric) taper.  A template whose two halves cancel is all zeros."""
     t = np.arange(length, dtype=np.float64) / fs
-    w = taper(length, taper_frac) * np.sin(2.0 * np.pi * (f0 * t + 0.5 * fdot * t * t))
-    return w / math.sqrt(float(np.dot(w, w)))
+    core = np.sin(2.0 * np.pi * (f0 * t + 0.5 * fdot * t * t))
+    if symmetric:
+        core = core + core[::-1]
+    w = taper(length, taper_frac) * core
+    norm = math.sqrt(float(np.dot(w, w)))
+    return w / norm if norm > 0.0 else w
 
 
-def chirp_bank(params: np.ndarray, fs: float, length: int, taper_frac: float) -> np.ndarray:
+def chirp_bank(params: np.ndarray, fs: float, length: int, taper_frac: float,
+               symmetric: bool = False) -> np.ndarray:
     """Templates for rows (f0, fdot) of ``params``; shape (K, length), FP64."""
-    return np.stack([chirp_template(f0, fd, fs, length, taper_frac) for f0, fd in params])
+    return np.stack([chirp_template(f0, fd, fs, length, taper_frac, symmetric)
+                     for f0, fd in params])
 
 
 # ----------------------------------------------------------------------------
