@@ -224,6 +224,18 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+# the sources the N = 2^16 FP32 correlate kernel is compiled from
+CORRELATE_SOURCES = ("bege_corr.cuh", "bege_fft.cuh", "bege_corr_s8.cu", "bege_internal.h")
+
+
+def correlate_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_1708_01609_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in CORRELATE_SOURCES:
+        h.update(open(os.path.join(src, name), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record(templates: int):
     """DRAM bytes per correlate launch from the committed ncu summary, if the
     kernel source is unchanged since it was captured; else None."""
@@ -233,12 +245,7 @@ def traffic_record(templates: int):
     rec = json.load(open(path)).get("correlate_kernel")
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1708_01609_gb300", "csrc")
-    h = hashlib.sha256()
-    for name in sorted(os.listdir(src)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(src, name), "rb").read())
-    if rec.get("source_sha256") != h.hexdigest():
+    if rec.get("source_sha256") != correlate_source_hash():
         return None
     return rec["dram_bytes_per_correlation"] * templates
 

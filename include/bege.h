@@ -105,6 +105,15 @@ int bege_load_segment_device(bege_ctx* ctx, const float* strain_dev, int64_t n,
 int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, double tau,
                      double taper_frac, void* stream, int32_t* bank_id);
 
+/* As bege_define_bank, with the time-symmetric chirps of the paper's banks
+ * (Fig. 2 caption: each chirp superposed with itself backward in time, for
+ * ascending and descending signals alike):
+ *     w_k[m] = T(m) (sin(2 pi phi(t_m)) + sin(2 pi phi(t_{L-1-m}))),
+ * phi(t) = f0 t + fdot t^2 / 2, scaled to unit L2 norm (all zeros if the
+ * two halves cancel).  Errors: as bege_define_bank. */
+int bege_define_bank_symmetric(bege_ctx* ctx, const bege_chirp* params, int64_t count,
+                               double tau, double taper_frac, void* stream, int32_t* bank_id);
+
 /* Template bank from explicit samples: `samples` is a HOST array of
  * count x length FP32 values, row-major, used as given (no normalisation). */
 int bege_define_bank_samples(bege_ctx* ctx, const float* samples, int64_t count,

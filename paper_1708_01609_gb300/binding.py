@@ -83,6 +83,8 @@ SIGNATURES = {
     "bege_load_segment_device": (ctypes.c_int, [_VP, _VP, _I64, _I32, _VP, _PI32]),
     "bege_define_bank": (ctypes.c_int, [_VP, _VP, _I64, ctypes.c_double, ctypes.c_double, _VP,
                                         _PI32]),
+    "bege_define_bank_symmetric": (ctypes.c_int, [_VP, _VP, _I64, ctypes.c_double, ctypes.c_double,
+                                                  _VP, _PI32]),
     "bege_define_bank_samples": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _PI32]),
     "bege_correlate": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
     "bege_correlate_max": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
@@ -207,11 +209,13 @@ class Context:
 
     # -- banks ------------------------------------------------------------
     def bege_define_bank(self, params: np.ndarray, tau: float = 1.0, taper_frac: float = 0.05,
-                         stream: int = 0) -> int:
+                         stream: int = 0, symmetric: bool = False) -> int:
+        """symmetric: bege_define_bank_symmetric (chirps forward + backward in time)."""
         p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 2)
         bid = _I32()
-        _check(self.lib.bege_define_bank(self.h, _ptr(p), len(p), tau, taper_frac, stream,
-                                         ctypes.byref(bid)), "bege_define_bank")
+        fn = self.lib.bege_define_bank_symmetric if symmetric else self.lib.bege_define_bank
+        _check(fn(self.h, _ptr(p), len(p), tau, taper_frac, stream, ctypes.byref(bid)),
+               "bege_define_bank_symmetric" if symmetric else "bege_define_bank")
         return bid.value
 
     def bege_define_bank_samples(self, samples: np.ndarray, stream: int = 0) -> int:

@@ -575,8 +575,8 @@ int bege_load_segment_device(bege_ctx* ctx, const float* strain_dev, int64_t n, 
   return segment_common(ctx, strain_dev, n, channel, static_cast<cudaStream_t>(stream), seg_id);
 }
 
-int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, double tau,
-                     double taper_frac, void* stream, int32_t* bank_id) {
+static int define_bank_impl(bege_ctx* ctx, const bege_chirp* params, int64_t count, double tau,
+                            double taper_frac, void* stream, int32_t* bank_id, bool symmetric) {
   if (!ctx || !params || !bank_id) return fail(BEGE_EINVAL, "NULL argument");
   if (count <= 0 || count > (int64_t)1 << 31) return fail(BEGE_EINVAL, "count out of range");
   if (!(tau > 0.0) || !std::isfinite(tau)) return fail(BEGE_EINVAL, "tau must be positive");
@@ -610,7 +610,7 @@ int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, dou
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = bege::launch_bank_chirp(static_cast<unsigned long long*>(dab.ptr), count, L, bank->Lp,
-                                taper_frac, static_cast<float*>(bank->w.ptr), s);
+                                taper_frac, symmetric, static_cast<float*>(bank->w.ptr), s);
   cudaError_t e2 = cudaStreamSynchronize(s);
   ctx->release(&dab);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -621,6 +621,16 @@ int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, dou
   ctx->banks[id] = std::move(bank);
   *bank_id = id;
   return BEGE_OK;
+}
+
+int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, double tau,
+                     double taper_frac, void* stream, int32_t* bank_id) {
+  return define_bank_impl(ctx, params, count, tau, taper_frac, stream, bank_id, false);
+}
+
+int bege_define_bank_symmetric(bege_ctx* ctx, const bege_chirp* params, int64_t count,
+                               double tau, double taper_frac, void* stream, int32_t* bank_id) {
+  return define_bank_impl(ctx, params, count, tau, taper_frac, stream, bank_id, true);
 }
 
 int bege_define_bank_samples(bege_ctx* ctx, const float* samples, int64_t count, int64_t length,

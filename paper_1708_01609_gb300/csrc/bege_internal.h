@@ -115,8 +115,10 @@ cudaError_t launch_correlate_tc(const PlanDev& p, const CorrelateArgs& a, int pr
                                 cudaStream_t s);
 
 // Bank synthesis: count chirps, phase coefficients alpha/beta as unsigned
-// 64-bit fixed point (cycles * 2^64), L samples, taper fraction; rows of Lp.
+// 64-bit fixed point (cycles * 2^64), L samples, taper fraction; rows of Lp;
+// symmetric: the chirp plus its time reversal (Fig. 2 caption).
 cudaError_t launch_bank_chirp(const unsigned long long* alpha_beta, int64_t count, int64_t L,
-                              int64_t Lp, double taper_frac, float* bank, cudaStream_t s);
+                              int64_t Lp, double taper_frac, bool symmetric, float* bank,
+                              cudaStream_t s);
 
 }  // namespace bege

@@ -81,15 +81,24 @@ cudaError_t launch_correlate(const PlanDev& p, const CorrelateArgs& a, CorrConfi
 }
 
 // ---------------------------------------------------------------------------
-// Bank synthesis: w[m] = T(m) sin(2 pi phase(m)), unit L2 norm
+// Bank synthesis: w[m] = T(m) sin(2 pi phase(m)), unit L2 norm; time-
+// symmetric banks (Fig. 2 caption): w[m] = T(m) (sin(2 pi phase(m)) +
+// sin(2 pi phase(L - 1 - m))), the chirp forward and backward in time.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double chirp_sample(unsigned long long alpha, unsigned long long beta,
-                                               int64_t m, int64_t L, int width, double denom) {
+__device__ __forceinline__ double chirp_sin(unsigned long long alpha, unsigned long long beta,
+                                            int64_t m) {
   const unsigned long long um = (unsigned long long)m;
   // phase in cycles * 2^64, exact modulo one cycle
   const unsigned long long ph = alpha * um + beta * (um * um);
   const double c = (double)(long long)ph * 0x1p-64;  // in [-1/2, 1/2)
-  const double s = sinpi(2.0 * c);
+  return sinpi(2.0 * c);
+}
+
+__device__ __forceinline__ double chirp_sample(unsigned long long alpha, unsigned long long beta,
+                                               int64_t m, int64_t L, int width, double denom,
+                                               bool symmetric) {
+  double s = chirp_sin(alpha, beta, m);
+  if (symmetric) s += chirp_sin(alpha, beta, L - 1 - m);
   const int64_t mm = m < L - 1 - m ? m : L - 1 - m;
   double t = 1.0;
   if (mm <= width) t = 0.5 * (1.0 - cospi(2.0 * (double)mm / denom));
@@ -98,6 +107,7 @@ __device__ __forceinline__ double chirp_sample(unsigned long long alpha, unsigne
 
 __global__ void __launch_bounds__(256) bank_chirp_kernel(const unsigned long long* __restrict__ ab,
                                                          int64_t L, int64_t Lp, double frac,
+                                                         bool symmetric,
                                                          float* __restrict__ bank) {
   __shared__ double red[8];
   const int64_t k = blockIdx.x;
@@ -106,7 +116,7 @@ __global__ void __launch_bounds__(256) bank_chirp_kernel(const unsigned long lon
   const double denom = frac * (double)(L - 1);
   double acc = 0.0;
   for (int64_t m = threadIdx.x; m < L; m += blockDim.x) {
-    const double v = chirp_sample(alpha, beta, m, L, width, denom);
+    const double v = chirp_sample(alpha, beta, m, L, width, denom, symmetric);
     acc = fma(v, v, acc);
   }
 #pragma unroll
@@ -118,13 +128,16 @@ __global__ void __launch_bounds__(256) bank_chirp_kernel(const unsigned long lon
   const double scale = norm > 0.0 ? 1.0 / sqrt(norm) : 0.0;
   float* row = bank + k * Lp;
   for (int64_t m = threadIdx.x; m < Lp; m += blockDim.x)
-    row[m] = m < L ? (float)(chirp_sample(alpha, beta, m, L, width, denom) * scale) : 0.f;
+    row[m] = m < L ? (float)(chirp_sample(alpha, beta, m, L, width, denom, symmetric) * scale)
+                   : 0.f;
 }
 
 cudaError_t launch_bank_chirp(const unsigned long long* alpha_beta, int64_t count, int64_t L,
-                              int64_t Lp, double taper_frac, float* bank, cudaStream_t s) {
+                              int64_t Lp, double taper_frac, bool symmetric, float* bank,
+                              cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  bank_chirp_kernel<<<(unsigned)count, 256, 0, s>>>(alpha_beta, L, Lp, taper_frac, bank);
+  bank_chirp_kernel<<<(unsigned)count, 256, 0, s>>>(alpha_beta, L, Lp, taper_frac, symmetric,
+                                                    bank);
   return cudaGetLastError();
 }
 
