@@ -207,6 +207,20 @@ def tails(rho: np.ndarray, sigma: float, kappa: float, k: int) -> np.ndarray:
     return out
 
 
+def tails_band(rho: np.ndarray, sigma: float, kappa_lo: float, kappa_hi: float,
+               k: int) -> np.ndarray:
+    """Eq. tail generalised to a finite band (Sec. 5, deep searches): every
+    (k, n, rho[n]) with kappa_lo sigma < |rho[n]| < kappa_hi sigma, by n."""
+    rho = np.asarray(rho, dtype=np.float64)
+    a = np.abs(rho)
+    lags = np.nonzero((a > kappa_lo * sigma) & (a < kappa_hi * sigma))[0]
+    out = np.empty(len(lags), dtype=TAIL_DTYPE)
+    out["tmpl"] = k
+    out["lag"] = lags
+    out["value"] = rho[lags]
+    return out
+
+
 def search(y: np.ndarray, templates: np.ndarray, kappa: float, k0: int = 0,
            batch: int = 32, return_rho: bool = False) -> dict:
     """Correlate segment ``y`` with every template row and keep the tails.

@@ -415,3 +415,24 @@ def test_symmetric_chirp_responds_to_both_directions():
     assert abs(r_up - r_down) < 1e-9 and r_up > 0.6
     plain_down = O.correlate_fft(up, y_down)[3000]
     assert O.correlate_fft(up, y_up)[3000] > 0.999 and abs(plain_down) < 0.1
+
+
+# ----------------------------------------------------------------------------
+# Band threshold (Sec. 5: Eq. tail over a finite band)
+# ----------------------------------------------------------------------------
+def test_tails_band_definition():
+    """Scalar check of kappa_lo sigma < |rho| < kappa_hi sigma, and the band
+    as the lower tails minus those at or above the upper bound; both ends
+    are excluded."""
+    g = np.random.default_rng(5)
+    rho = g.standard_normal(500) * 2.0
+    sigma = 1.25
+    rho[10], rho[11], rho[12] = 4.0 * sigma, -5.0 * sigma, 4.5 * sigma  # on the bounds, inside
+    band = O.tails_band(rho, sigma, 4.0, 5.0, 9)
+    want = [n for n in range(500) if 4.0 * sigma < abs(rho[n]) < 5.0 * sigma]
+    assert band["lag"].tolist() == want
+    assert np.all(band["tmpl"] == 9) and np.array_equal(band["value"], rho[want])
+    assert 10 not in want and 11 not in want and 12 in want
+    lo = O.tails(rho, sigma, 4.0, 9)
+    hi = set(np.nonzero(np.abs(rho) >= 5.0 * sigma)[0].tolist())
+    assert band["lag"].tolist() == [n for n in lo["lag"].tolist() if n not in hi]
