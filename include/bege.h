@@ -150,6 +150,15 @@ int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capa
 int bege_correlate_max(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
                        int64_t k_end, float kappa, void* stream, int32_t* job_id);
 
+/* As bege_correlate, with the tails restricted to a finite band (Sec. 5,
+ * for deep searches with a low threshold): records (k, n, rho_k[n]) with
+ * kappa_lo sigma_k < |rho_k[n]| < kappa_hi sigma_k.  Fetch them with
+ * bege_fetch_tails.  Errors: as bege_correlate; EINVAL unless
+ * 0 <= kappa_lo < kappa_hi, both finite. */
+int bege_correlate_band(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                        int64_t k_end, float kappa_lo, float kappa_hi, void* stream,
+                        int32_t* job_id);
+
 /* Wait for a bege_correlate_max job and copy its projection to HOST arrays
  * of n = N entries: snr[n] = rho / sigma of the kept hit and tmpl[n] its
  * template index, or snr 0 and tmpl -1 where no template passes.

@@ -89,6 +89,8 @@ SIGNATURES = {
     "bege_correlate": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
     "bege_correlate_max": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
     "bege_fetch_max": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64]),
+    "bege_correlate_band": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float,
+                                           ctypes.c_float, _VP, _PI32]),
     "bege_fetch_tails": (ctypes.c_int, [_VP, _I32, _VP, _I64, _PI64, _PI64]),
     "bege_sort_tails": (ctypes.c_int, [_VP, _I64]),
     "bege_query": (ctypes.c_int, [_VP, _I32]),
@@ -240,6 +242,13 @@ class Context:
         jid = _I32()
         _check(self.lib.bege_correlate_max(self.h, seg, bank, k_begin, k_end, kappa, stream,
                                            ctypes.byref(jid)), "bege_correlate_max")
+        return jid.value
+
+    def bege_correlate_band(self, seg: int, bank: int, k_begin: int, k_end: int, kappa_lo: float,
+                            kappa_hi: float, stream: int = 0) -> int:
+        jid = _I32()
+        _check(self.lib.bege_correlate_band(self.h, seg, bank, k_begin, k_end, kappa_lo, kappa_hi,
+                                            stream, ctypes.byref(jid)), "bege_correlate_band")
         return jid.value
 
     def bege_fetch_max(self, job: int, n: int):

@@ -664,7 +664,7 @@ int bege_define_bank_samples(bege_ctx* ctx, const float* samples, int64_t count,
 
 static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
                           int64_t k_end, float kappa, cudaStream_t s, float* dump_dev,
-                          int32_t* job_id, bool project = false) {
+                          int32_t* job_id, bool project = false, float kappa_hi = 0.f) {
   auto si = ctx->segs.find(seg_id);
   if (si == ctx->segs.end()) return fail(BEGE_EINVAL, "unknown segment handle");
   auto bi = ctx->banks.find(bank_id);
@@ -720,6 +720,7 @@ static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
     a.max_clusters = 0;
     a.status = reinterpret_cast<unsigned int*>(static_cast<char*>(job->buf->counter.ptr) + 8);
     a.proj = static_cast<unsigned long long*>(job->proj.ptr);
+    a.kappa_hi = kappa_hi;
     if (ctx->cfg.precision != 0) {
       e = bege::launch_correlate_tc(seg->plan->dev, a, ctx->cfg.precision, s);
     } else {
@@ -759,6 +760,18 @@ int bege_correlate_max(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k
   std::lock_guard<std::mutex> lk(ctx->mu);
   return correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, kappa,
                         static_cast<cudaStream_t>(stream), nullptr, job_id, true);
+}
+
+int bege_correlate_band(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                        int64_t k_end, float kappa_lo, float kappa_hi, void* stream,
+                        int32_t* job_id) {
+  if (!ctx || !job_id) return fail(BEGE_EINVAL, "NULL argument");
+  if (!std::isfinite(kappa_lo) || !std::isfinite(kappa_hi) || !(kappa_hi > kappa_lo))
+    return fail(BEGE_EINVAL, "the band needs finite kappa_lo < kappa_hi");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, kappa_lo,
+                        static_cast<cudaStream_t>(stream), nullptr, job_id, false, kappa_hi);
 }
 
 int bege_fetch_max(bege_ctx* ctx, int32_t job_id, float* snr, int32_t* tmpl, int64_t n) {

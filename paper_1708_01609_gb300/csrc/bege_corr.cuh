@@ -542,14 +542,19 @@ struct TailOut {
   // optional per-lag maximum over the bank (Eq. Ak): one 64-bit word per
   // lag, (bits of rho/sigma) << 32 | ~template, raised with atomicMax
   unsigned long long* proj = nullptr;
+  // optional upper end of a tail band (Sec. 5): keep |rho| < kappa_hi sigma
+  // as well; 0 = no upper end
+  float kappa_hi = 0.f;
 };
 
-// PROJ: also raise the per-lag maximum a.proj (compiled only into the kernels
-// that serve bege_correlate_max, so the others keep their code unchanged).
-template <int F, int S, int NC, int T, bool PROJ = false>
+// EXT: the extended epilogue, the per-lag maximum a.proj and the band's
+// upper end a.kappa_hi (compiled only into the kernels that serve
+// bege_correlate_max and bege_correlate_band, so the others keep their code
+// unchanged).  sigma: the template's sigma (thr = kappa sigma).
+template <int F, int S, int NC, int T, bool EXT = false>
 __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, int rank, float thr,
                                                  uint32_t tmpl, int64_t krow, const TailOut& a,
-                                                 float inv_sigma, int tix = threadIdx.x) {
+                                                 float sigma, int tix = threadIdx.x) {
   constexpr int C = ColMap<S, NC>::C;
   constexpr int per = F / C;
   static_assert(per % T == 0, "combine rounds");
@@ -558,6 +563,8 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
   // so the unscaled values are tested and only the emitted ones are scaled
   const float invH = 1.0f / (float)H;
   const float thrH = thr * (float)H;
+  // |t / H| < kappa_hi sigma exactly when |t| < kappa_hi sigma H (H a power of two)
+  const float hiH = (EXT && a.kappa_hi > 0.f) ? a.kappa_hi * sigma * (float)H : INFINITY;
 #pragma unroll 1
   for (int it = 0; it < per / T; ++it) {
     const int n1 = rank * per + it * T + tix;
@@ -578,8 +585,14 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
       uint32_t mask = 0;
 #pragma unroll
       for (int n2 = 0; n2 < S; ++n2) {
-        mask |= (fabsf(t[n2].x) > thrH ? 1u : 0u) << (2 * n2);
-        mask |= (fabsf(t[n2].y) > thrH ? 1u : 0u) << (2 * n2 + 1);
+        if constexpr (EXT) {
+          const float ax = fabsf(t[n2].x), ay = fabsf(t[n2].y);
+          mask |= (ax > thrH && ax < hiH ? 1u : 0u) << (2 * n2);
+          mask |= (ay > thrH && ay < hiH ? 1u : 0u) << (2 * n2 + 1);
+        } else {
+          mask |= (fabsf(t[n2].x) > thrH ? 1u : 0u) << (2 * n2);
+          mask |= (fabsf(t[n2].y) > thrH ? 1u : 0u) << (2 * n2 + 1);
+        }
       }
       const int cnt = __popc(mask);
       int incl = cnt;
@@ -605,14 +618,14 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
               r->value = (e ? t[n2].y : t[n2].x) * invH;
             }
             ++pos;
-            if constexpr (PROJ) {
+            if constexpr (EXT) {
               // positive values above the threshold: v > thr > 0, so the
               // bits of v / sigma order like the values; equal values keep
               // the smaller template (larger ~tmpl)
               const float v = (e ? t[n2].y : t[n2].x) * invH;
               if (a.proj && v > thr)
                 atomicMax(a.proj + (2 * (n1 + F * n2) + e),
-                          ((unsigned long long)__float_as_uint(v * inv_sigma) << 32) |
+                          ((unsigned long long)__float_as_uint(v * (1.0f / sigma)) << 32) |
                               (unsigned long long)(~tmpl));
             }
           }
@@ -709,7 +722,7 @@ __device__ __forceinline__ float group_sigma(float* sigpart, int gbase, int N) {
   return sqrtf(2.0f * tot) / (float)N;
 }
 
-template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool PROJ>
+template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool EXT>
 __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, CorrelateArgs a) {
   constexpr int C = ColMap<S, NC>::C;
   cg::cluster_group cluster = cg::this_cluster();
@@ -723,7 +736,7 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
   const int ncl = gridDim.x / C;
   const int nz = (int)(a.Lp / 2);
   const int nfold = (nz + F - 1) / F;
-  const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj};
+  const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj, a.kappa_hi};
 
   for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
     template_columns<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold, a.AB);
@@ -732,8 +745,8 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
     const int64_t krow = k - a.k0;
     if (rank == 0 && threadIdx.x == 0) a.sigma[krow] = sigma;
     // S6: S-point combine, threshold, warp-ballot compaction
-    combine_and_emit<F, S, NC, T, PROJ>(Smem<F, NC>::colptr(), H, rank, a.kappa * sigma,
-                                        (uint32_t)k, krow, out, PROJ ? 1.0f / sigma : 0.f);
+    combine_and_emit<F, S, NC, T, EXT>(Smem<F, NC>::colptr(), H, rank, a.kappa * sigma,
+                                       (uint32_t)k, krow, out, sigma);
     cluster.sync();  // remote reads done before the columns are overwritten
   }
 }
@@ -746,11 +759,11 @@ static cudaError_t ensure_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool PROJ>
+template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool EXT>
 static cudaError_t launch_corr_tp(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
   constexpr int C = ColMap<S, NC>::C;
   constexpr size_t smem = Lay<F, NC>::total;
-  auto kern = correlate_kernel<F, S, NC, T, MINB, HALFZ, PROJ>;
+  auto kern = correlate_kernel<F, S, NC, T, MINB, HALFZ, EXT>;
   cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -781,11 +794,12 @@ static cudaError_t launch_corr_tp(const PlanDev& p, const CorrelateArgs& a, cuda
   return cudaLaunchKernelEx(&cfg, kern, p, a);
 }
 
-// The projection epilogue (bege_correlate_max) runs in its own instantiation.
+// The extended epilogue (bege_correlate_max, bege_correlate_band) runs in
+// its own instantiation.
 template <int F, int S, int NC, int T, int MINB, bool HALFZ>
 static cudaError_t launch_corr_t(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
-  return a.proj ? launch_corr_tp<F, S, NC, T, MINB, HALFZ, true>(p, a, s)
-                : launch_corr_tp<F, S, NC, T, MINB, HALFZ, false>(p, a, s);
+  return (a.proj || a.kappa_hi > 0.f) ? launch_corr_tp<F, S, NC, T, MINB, HALFZ, true>(p, a, s)
+                                      : launch_corr_tp<F, S, NC, T, MINB, HALFZ, false>(p, a, s);
 }
 
 template <int F, int S, int NC, int T>

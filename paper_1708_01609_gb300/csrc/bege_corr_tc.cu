@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
   const int cid = blockIdx.x / C;
   const int ncl = gridDim.x / C;
   const int nz = (int)(a.Lp / 2);
-  const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj};
+  const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj, a.kappa_hi};
   uint32_t parity = 0;
   bool ok = true;
   const int warp = tid >> 5, lane = tid & 31;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
       const float sigma = sqrtf(2.0f * SM::sigpart()[g]) / (float)N;
       if (lt == 0) a.sigma[krow] = sigma;
       combine_and_emit<kF, S, NC, kGT, true>(SM::colptr() + S * g, H, 0, a.kappa * sigma,
-                                             (uint32_t)k, krow, out, 1.0f / sigma, lt);
+                                             (uint32_t)k, krow, out, sigma, lt);
       group_sync(g);  // reads done before the region is overwritten
     } else {
       cluster.sync();  // every column and sigma partial of the cluster is ready
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
       const float sigma = sqrtf(2.0f * tot) / (float)N;
       if (rank == 0 && tid == 0) a.sigma[krow] = sigma;
       combine_and_emit<kF, S, NC, T, true>(SM::colptr(), H, rank, a.kappa * sigma, (uint32_t)k,
-                                           krow, out, 1.0f / sigma);
+                                           krow, out, sigma);
       cluster.sync();  // remote reads done before the regions are overwritten
     }
   }

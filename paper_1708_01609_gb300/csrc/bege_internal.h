@@ -92,6 +92,7 @@ struct CorrelateArgs {
   int max_clusters;      // 0 = as many as fit
   unsigned int* status;  // optional: set non-zero by a kernel whose bounded wait gave up
   unsigned long long* proj = nullptr;  // optional: per-lag maximum over the bank (Eq. Ak)
+  float kappa_hi = 0.f;                // optional: tails only below kappa_hi sigma (0 = none)
 };
 cudaError_t launch_correlate(const PlanDev& p, const CorrelateArgs& a, CorrConfig cfg,
                              cudaStream_t s);

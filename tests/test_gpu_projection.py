@@ -112,3 +112,38 @@ def test_fetch_max_rejects_plain_jobs_and_wrong_length():
     with pytest.raises(BegeError):
         ctx.bege_fetch_max(job, len(seg_data.y) // 2)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_band_tails_match_oracle(prec):
+    """Tails over a finite band (Sec. 5): kappa_lo sigma < |rho| < kappa_hi
+    sigma on the N = 2^14 case, against the oracle; entries within the
+    tolerance band of either end are excluded from set parity."""
+    seg_data, params = S.small_case()
+    lo, hi = 3.5, 4.25
+    ctx = make_ctx(tail_capacity=1 << 20, precision=prec)
+    seg = ctx.bege_load_segment(seg_data.y)
+    bid = ctx.bege_define_bank(params)
+    job = ctx.bege_correlate_band(seg, bid, 0, len(params), lo, hi)
+    recs, total = ctx.bege_fetch_tails(job)
+    ctx.close()
+    assert total == len(recs)
+    bank = O.chirp_bank(params, 4096.0, 4096, 0.05)
+    rho, sig = oracle_rho(seg_data.y, bank)
+    tol = 1e-5 if prec == 0 else 2e-3
+    near = max(1e-3, tol)
+    got = {(int(t), int(l)): float(v) for t, l, v in zip(recs["tmpl"], recs["lag"], recs["value"])}
+    n_ref = 0
+    for k in range(len(params)):
+        ref = O.tails_band(rho[k], sig[k], lo, hi, k)
+        for n, v in zip(ref["lag"], ref["value"]):
+            a = abs(v) / sig[k]
+            if (k, int(n)) not in got:
+                assert min(abs(a - lo), abs(a - hi)) <= near, (k, n, a)
+                continue
+            n_ref += 1
+            assert abs(got[(k, int(n))] - v) <= tol * sig[k]
+    for (k, n), v in got.items():
+        a = abs(rho[k][n]) / sig[k]
+        assert lo - near <= a <= hi + near, (k, n, a)
+    assert n_ref > 300  # ~470 expected from noise alone, plus the injection
