@@ -294,6 +294,45 @@ def table3_rows(snr: np.ndarray, tmpl: np.ndarray, f0: np.ndarray) -> np.ndarray
     return rows
 
 
+def coincidences(tmpl1: np.ndarray, tmpl2: np.ndarray, f0: np.ndarray,
+                 delta: float = 50.0) -> dict:
+    """Simultaneous hits of two channels (Sec. 5: H1 and L1 at the same
+    sample offset), from their per-lag projections (tmpl -1 = no hit): the
+    counts of each channel, of lags where both hit, and of those whose
+    templates' initial frequencies differ by less than delta [Hz]."""
+    n1 = n2 = both = near = 0
+    lags = []
+    for n in range(len(tmpl1)):
+        a, b = int(tmpl1[n]), int(tmpl2[n])
+        n1 += a >= 0
+        n2 += b >= 0
+        if a >= 0 and b >= 0:
+            both += 1
+            if abs(float(f0[a]) - float(f0[b])) < delta:
+                near += 1
+                lags.append(n)
+    return {"hits": (n1, n2), "simultaneous": both, "within_delta": near,
+            "lags": np.array(lags, dtype=np.int64)}
+
+
+def table3_rows_two(snr1, tmpl1, snr2, tmpl2, f0) -> np.ndarray:
+    """Table 3 with both channels: one row per lag where either hits, with
+    1000 rho and f0 of each channel and zeros for a channel without a hit."""
+    rows = []
+    for n in range(len(tmpl1)):
+        a, b = int(tmpl1[n]), int(tmpl2[n])
+        if a < 0 and b < 0:
+            continue
+        rows.append((n + 1,
+                     math.floor(1000.0 * float(snr1[n])) if a >= 0 else 0,
+                     math.floor(1000.0 * float(snr2[n])) if b >= 0 else 0,
+                     math.floor(float(f0[a])) if a >= 0 else 0,
+                     math.floor(float(f0[b])) if b >= 0 else 0))
+    return np.array(rows, dtype=[("offset", np.int64), ("rho1000_1", np.int32),
+                                 ("rho1000_2", np.int32), ("f0_1", np.int32),
+                                 ("f0_2", np.int32)])
+
+
 def near_threshold(values: np.ndarray, sigma: np.ndarray, kappa: float,
                    band: float = 1e-3) -> np.ndarray:
     """True where ||rho| - kappa sigma| <= band * sigma (excluded from set parity)."""

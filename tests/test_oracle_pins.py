@@ -436,3 +436,31 @@ def test_tails_band_definition():
     lo = O.tails(rho, sigma, 4.0, 9)
     hi = set(np.nonzero(np.abs(rho) >= 5.0 * sigma)[0].tolist())
     assert band["lag"].tolist() == [n for n in lo["lag"].tolist() if n not in hi]
+
+
+# ----------------------------------------------------------------------------
+# Two channels: simultaneous hits and Table 3 (Sec. 5)
+# ----------------------------------------------------------------------------
+def test_coincidences_worked_example():
+    f0 = np.array([400.0, 440.0, 460.0, 1000.0])
+    t1 = np.array([-1, 0, 1, 3, -1, 2])
+    t2 = np.array([1, 1, -1, 2, -1, 2])
+    c = O.coincidences(t1, t2, f0, delta=50.0)
+    assert c["hits"] == (4, 4)
+    assert c["simultaneous"] == 3              # lags 1, 3, 5
+    assert c["within_delta"] == 2              # lag 1 (40 Hz) and lag 5 (0 Hz); lag 3 is 540 Hz
+    assert c["lags"].tolist() == [1, 5]
+    assert O.coincidences(t1, t2, f0, delta=40.0)["within_delta"] == 1   # strict
+
+
+def test_table3_two_channel_rows():
+    """The three rows Table 3 prints (1000 rho and f0 per channel, zeros for
+    no hit: 0/5522/0/1988, 5747/0/486/0, 5516/0/623/0), rebuilt from
+    projections with those values at offsets renumbered 1..3."""
+    f0 = np.array([486.4, 623.9, 1988.2])
+    s1 = np.array([0.0, 5.7471, 5.5169, 0.0])
+    t1 = np.array([-1, 0, 1, -1])
+    s2 = np.array([5.5229, 0.0, 0.0, 0.0])
+    t2 = np.array([2, -1, -1, -1])
+    rows = O.table3_rows_two(s1, t1, s2, t2, f0)
+    assert rows.tolist() == [(1, 0, 5522, 0, 1988), (2, 5747, 0, 486, 0), (3, 5516, 0, 623, 0)]
