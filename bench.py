@@ -363,6 +363,8 @@ def run_ours(args):
         "clocks": clk,
         "tails_per_step": statistics.mean(tails),
     }
+    if rank == 0 and world == 1 and args.precision == "fp32":
+        line["fft_normalized"] = fft_normalized(kernel_ms, templates)
     if rank == 0 and world == 1 and args.precision == "fp32" and not args.no_precision_form:
         line["max_projection"] = max_projection_form(ctx, bank, y_dev, templates, args, value,
                                                      stream_obj)
@@ -380,6 +382,41 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def fft_normalized(kernel_ms: float, templates: int, batch: int = 2048, reps: int = 10) -> dict:
+    """The paper's efficiency measure (Sec. 4: ~65%, 'normalised to FFT
+    alone'): the time the vendor FFT library needs for one correlation's
+    transforms, a forward and an inverse real FFT of N = 2^16 (cuFFT through
+    torch.fft, batched, device-resident), divided by the correlate kernel's
+    time per correlation.  Context for the roofline, not a replacement."""
+    import torch
+    x = torch.randn(batch, N_SAMPLES, device="cuda", dtype=torch.float32)
+    spec = torch.fft.rfft(x)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / batch * 1e3  # us per transform
+
+    t_r2c = timed(lambda: torch.fft.rfft(x))
+    t_c2r = timed(lambda: torch.fft.irfft(spec, n=N_SAMPLES))
+    t_corr = kernel_ms / templates * 1e3
+    del x, spec
+    torch.cuda.empty_cache()
+    return {"cufft_rfft_us": t_r2c, "cufft_irfft_us": t_c2r, "correlation_us": t_corr,
+            "efficiency": (t_r2c + t_c2r) / t_corr,
+            "basis": "cuFFT R2C + C2R of N=2^16 (batch 2048, FP32, device-resident) per "
+                     "correlation / correlate kernel time per correlation (the paper's "
+                     "'efficiency normalised to FFT alone', Sec. 4)"}
 
 
 def max_projection_form(ctx, bank: int, y_dev, templates: int, args, fp32_value: float,
