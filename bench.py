@@ -368,6 +368,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and args.precision == "fp32" and not args.no_precision_form:
         line["max_projection"] = max_projection_form(ctx, bank, y_dev, templates, args, value,
                                                      stream_obj)
+        line["multi_segment"] = multi_segment_form(ctx, bank, templates, value)
         ctx.close()
         ctx = None
         line["precision_form"] = {
@@ -419,6 +420,31 @@ def fft_normalized(kernel_ms: float, templates: int, batch: int = 2048, reps: in
                      "normalisation pass; the C2R time includes the library's copy of its "
                      "input) per correlation / correlate kernel time per correlation (the "
                      "paper's 'efficiency normalised to FFT alone', Sec. 4)"}
+
+
+def multi_segment_form(ctx, bank: int, templates: int, fp32_value: float, m: int = 8,
+                       reps: int = 3) -> dict:
+    """The paper's block of segments per template (Sec. 3.2): m segments of
+    N = 2^16 against the whole bank in one bege_correlate_multi launch, the
+    template transforms shared; kernel time per launch (CUDA events around it)."""
+    segs = [ctx.bege_load_segment(S.band_limited_noise(N_SAMPLES, 4000 + i)) for i in range(m)]
+    times = []
+    for r in range(reps + 1):
+        jobs = ctx.bege_correlate_multi(segs, bank, 0, templates, KAPPA)
+        for j in jobs:
+            ctx.bege_fetch_tails(j, capacity=0)
+        if r > 0:
+            times.append(ctx.bege_job_kernel_ms(jobs[0]))
+        for j in jobs:
+            ctx.bege_release(j)
+    for sg in segs:
+        ctx.bege_release(sg)
+    ms = statistics.median(times)
+    value = m * templates / (ms / 1e3)
+    return {"segments": m, "value": value, "unit": UNIT, "kernel_ms": ms,
+            "vs_fp32_path": value / fp32_value,
+            "note": "one launch for m segments: forward template transforms once, product, "
+                    "inverse and tails per segment; results bitwise those of single searches"}
 
 
 def max_projection_form(ctx, bank: int, y_dev, templates: int, args, fp32_value: float,

@@ -136,6 +136,20 @@ int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_beg
 int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capacity,
                      int64_t* n_written, int64_t* n_total);
 
+/* Several segments of one length against the same template range (Sec. 3.2:
+ * a template's transform serves a block of segments, steps ii-iv): per
+ * template the forward transform runs once, then each segment's product,
+ * inverse transform, sigma and tails follow with the arithmetic of
+ * bege_correlate, so every result is bitwise the single search's.  Writes
+ * one job handle per segment to job_ids[n_seg] (fetch, sigma and release as
+ * usual; the jobs finish together).  1 <= n_seg <= 8; FP32 contexts only;
+ * N >= 2^14 and templates of at most 4096 samples.  Extra device memory
+ * while the jobs live: 64 KB per resident CTA (about 20 MB).
+ * Errors: EINVAL, EBUDGET, ENOMEM, ECUDA. */
+int bege_correlate_multi(bege_ctx* ctx, const int32_t* seg_ids, int32_t n_seg, int32_t bank_id,
+                         int64_t k_begin, int64_t k_end, float kappa, void* stream,
+                         int32_t* job_ids);
+
 /* As bege_correlate, and the job also projects its hits onto one array of
  * the segment's N lags, keeping per lag the largest normalised value over
  * the bank (Eq. Ak over the templates, gathered as in Eq. Aa / Eq. BA with

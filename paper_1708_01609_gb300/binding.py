@@ -88,6 +88,8 @@ SIGNATURES = {
     "bege_define_bank_samples": (ctypes.c_int, [_VP, _VP, _I64, _I64, _VP, _PI32]),
     "bege_correlate": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
     "bege_correlate_max": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP, _PI32]),
+    "bege_correlate_multi": (ctypes.c_int, [_VP, _VP, _I32, _I32, _I64, _I64, ctypes.c_float, _VP,
+                                            _VP]),
     "bege_fetch_max": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64]),
     "bege_correlate_band": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float,
                                            ctypes.c_float, _VP, _PI32]),
@@ -236,6 +238,15 @@ class Context:
         _check(self.lib.bege_correlate(self.h, seg, bank, k_begin, k_end, kappa, stream,
                                        ctypes.byref(jid)), "bege_correlate")
         return jid.value
+
+    def bege_correlate_multi(self, segs, bank: int, k_begin: int, k_end: int, kappa: float,
+                             stream: int = 0) -> list[int]:
+        """One launch for several segments of one length; a job per segment."""
+        ids = np.ascontiguousarray(segs, dtype=np.int32)
+        out = np.empty(len(ids), dtype=np.int32)
+        _check(self.lib.bege_correlate_multi(self.h, _ptr(ids), len(ids), bank, k_begin, k_end,
+                                             kappa, stream, _ptr(out)), "bege_correlate_multi")
+        return out.tolist()
 
     def bege_correlate_max(self, seg: int, bank: int, k_begin: int, k_end: int, kappa: float,
                            stream: int = 0) -> int:

@@ -87,6 +87,7 @@ struct Job {
   std::unique_ptr<JobBuffers> buf;
   DevBuf proj;        // per-lag maximum over the bank (bege_correlate_max), n_proj words
   int64_t n_proj = 0;
+  DevBuf scratch;     // bege_correlate_multi: the group's template-spectrum scratch
   cudaEvent_t done = nullptr;
   cudaEvent_t k_start = nullptr, k_stop = nullptr;  // around the correlate kernel
 };
@@ -516,6 +517,7 @@ int bege_destroy(bege_ctx* ctx) {
       if (kv.second->done) cudaEventSynchronize(kv.second->done);
       destroy_job_events(kv.second.get());
       ctx->release(&kv.second->proj);
+      ctx->release(&kv.second->scratch);
       ctx->release(&kv.second->buf->sigma);
       ctx->release(&kv.second->buf->recs);
       ctx->release(&kv.second->buf->counter);
@@ -751,6 +753,97 @@ int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_beg
   std::lock_guard<std::mutex> lk(ctx->mu);
   return correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, kappa,
                         static_cast<cudaStream_t>(stream), nullptr, job_id);
+}
+
+int bege_correlate_multi(bege_ctx* ctx, const int32_t* seg_ids, int32_t n_seg, int32_t bank_id,
+                         int64_t k_begin, int64_t k_end, float kappa, void* stream,
+                         int32_t* job_ids) {
+  if (!ctx || !seg_ids || !job_ids) return fail(BEGE_EINVAL, "NULL argument");
+  if (n_seg < 1 || n_seg > bege::kMaxMulti)
+    return fail(BEGE_EINVAL, "between 1 and " + std::to_string(bege::kMaxMulti) + " segments");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->cfg.precision != 0)
+    return fail(BEGE_EINVAL, "the multi-segment search runs the FP32 path (precision 0)");
+  auto bi = ctx->banks.find(bank_id);
+  if (bi == ctx->banks.end()) return fail(BEGE_EINVAL, "unknown bank handle");
+  Bank* bank = bi->second.get();
+  if (k_begin < 0 || k_end > bank->count || k_begin >= k_end)
+    return fail(BEGE_EINVAL, "template range outside the bank or empty");
+  if (!std::isfinite(kappa) || kappa < 0.f) return fail(BEGE_EINVAL, "kappa must be finite, >= 0");
+  std::vector<Segment*> segs;
+  for (int32_t i = 0; i < n_seg; ++i) {
+    auto si = ctx->segs.find(seg_ids[i]);
+    if (si == ctx->segs.end()) return fail(BEGE_EINVAL, "unknown segment handle");
+    segs.push_back(si->second.get());
+  }
+  const int64_t n = segs[0]->n;
+  for (Segment* sg : segs)
+    if (sg->n != n) return fail(BEGE_EINVAL, "the segments must have one length");
+  if (n < (1 << 14) || bank->Lp > 4096 || bank->L > n)
+    return fail(BEGE_EINVAL, "the multi-segment search needs N >= 2^14 and templates of at "
+                             "most 4096 samples");
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "device attribute");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<std::unique_ptr<Job>> jobs;
+  auto unwind = [&](int rc) {
+    for (auto& j : jobs) {
+      destroy_job_events(j.get());
+      ctx->release(&j->scratch);
+      if (j->buf) ctx->pool.push_back(std::move(j->buf));
+    }
+    return rc;
+  };
+  for (int32_t i = 0; i < n_seg; ++i) {
+    auto job = std::make_unique<Job>();
+    job->seg = seg_ids[i];
+    job->bank = bank_id;
+    job->k0 = k_begin;
+    job->k1 = k_end;
+    job->kappa = kappa;
+    jobs.push_back(std::move(job));
+    Job* j = jobs.back().get();
+    int rc = take_job_buffers(ctx, k_end - k_begin, ctx->cfg.tail_capacity, &j->buf);
+    if (rc) return unwind(rc);
+    e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&j->k_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&j->k_stop);
+    if (e == cudaSuccess) e = cudaMemsetAsync(j->buf->counter.ptr, 0, 16, s);
+    if (e != cudaSuccess) return unwind(cuda_fail(e, "multi-segment job"));
+  }
+  int rc = ctx->alloc(&jobs[0]->scratch, bege::multi_scratch_bytes(sms));
+  if (rc) return unwind(rc);
+  bege::MultiArgs a{};
+  a.bank = static_cast<const float*>(bank->w.ptr);
+  a.Lp = bank->Lp;
+  a.k0 = k_begin;
+  a.k1 = k_end;
+  a.kappa = kappa;
+  a.M = n_seg;
+  for (int32_t i = 0; i < n_seg; ++i) {
+    a.AB[i] = static_cast<const float4*>(segs[i]->AB.ptr);
+    a.sigma[i] = static_cast<float*>(jobs[i]->buf->sigma.ptr);
+    a.recs[i] = static_cast<bege_tail*>(jobs[i]->buf->recs.ptr);
+    a.cap[i] = jobs[i]->buf->rec_cap;
+    a.counter[i] = static_cast<unsigned long long*>(jobs[i]->buf->counter.ptr);
+  }
+  a.scratch = static_cast<float2*>(jobs[0]->scratch.ptr);
+  for (auto& j : jobs)
+    if (e == cudaSuccess) e = cudaEventRecord(j->k_start, s);
+  if (e == cudaSuccess) e = bege::launch_correlate_multi(segs[0]->plan->dev, a, s);
+  for (auto& j : jobs) {
+    if (e == cudaSuccess) e = cudaEventRecord(j->k_stop, s);
+    if (e == cudaSuccess) e = cudaEventRecord(j->done, s);
+  }
+  if (e != cudaSuccess) return unwind(cuda_fail(e, "multi-segment correlate"));
+  for (int32_t i = 0; i < n_seg; ++i) {
+    const int32_t id = ctx->next_id++;
+    ctx->jobs[id] = std::move(jobs[i]);
+    job_ids[i] = id;
+  }
+  return BEGE_OK;
 }
 
 int bege_correlate_max(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
@@ -1326,6 +1419,7 @@ int bege_release(bege_ctx* ctx, int32_t handle) {
     cudaEventSynchronize(ji->second->done);
     destroy_job_events(ji->second.get());
     ctx->release(&ji->second->proj);
+    ctx->release(&ji->second->scratch);
     ctx->pool.push_back(std::move(ji->second->buf));
     ctx->jobs.erase(ji);
     return BEGE_OK;

@@ -359,9 +359,16 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Returns this thread's sum of |Y|^2; ends with the stores of inverse pass 1
 // (callers synchronise before reading the columns).
 // ---------------------------------------------------------------------------
-template <int S, int NC, int T>
+//
+// MULTI (several segments against one template): the forward half's output
+// Z (za, zb) is kept in `scratch` (this thread's 32 values, stride T; none
+// for a single segment); with `reload` the forward half is skipped and Z is
+// read back from there.
+template <int S, int NC, int T, bool MULTI = false>
 __device__ __forceinline__ float fused_mid(int rank, const float4* __restrict__ AB,
-                                           float* red_warp, int s_rt = S) {
+                                           float* red_warp, int s_rt = S,
+                                           float2* __restrict__ scratch = nullptr,
+                                           bool reload = false) {
   constexpr int F = 4096;
   using SM = Smem<F, NC>;
   constexpr int UPC = S == 1 ? 1 : NC / 2;
@@ -390,22 +397,37 @@ __device__ __forceinline__ float fused_mid(int rank, const float4* __restrict__ 
   float2 za[16], zb[16];
   float acc = 0.f;
   if (act) {
-    const float2* pa = SM::col(sa) + pad(ja);
-    const float2* pb = SM::col(sb) + pad(jb);
+    if (MULTI && reload) {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      za[r] = pa[r * step];
-      zb[r] = pb[r * step];
-    }
-    const float2* ta = SM::tw3() + ja;
-    const float2* tb = SM::tw3() + jb;
+      for (int r = 0; r < 16; ++r) {
+        za[r] = __ldcg(scratch + r * T + t);
+        zb[r] = __ldcg(scratch + (16 + r) * T + t);
+      }
+    } else {
+      const float2* pa = SM::col(sa) + pad(ja);
+      const float2* pb = SM::col(sb) + pad(jb);
 #pragma unroll
-    for (int r = 1; r < 16; ++r) {
-      za[r] = cmul(za[r], ta[r * 256]);
-      zb[r] = cmul(zb[r], tb[r * 256]);
+      for (int r = 0; r < 16; ++r) {
+        za[r] = pa[r * step];
+        zb[r] = pb[r * step];
+      }
+      const float2* ta = SM::tw3() + ja;
+      const float2* tb = SM::tw3() + jb;
+#pragma unroll
+      for (int r = 1; r < 16; ++r) {
+        za[r] = cmul(za[r], ta[r * 256]);
+        zb[r] = cmul(zb[r], tb[r * 256]);
+      }
+      dft<16, false>(za);
+      dft<16, false>(zb);
+      if (MULTI && scratch) {  // kept for the block's other segments
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          __stcg(scratch + r * T + t, za[r]);
+          __stcg(scratch + (16 + r) * T + t, zb[r]);
+        }
+      }
     }
-    dft<16, false>(za);
-    dft<16, false>(zb);
     const float4* aba = AB + ba * F + ja;
     const float4* abb = AB + bb * F + jb;
     if (!self0) {

@@ -97,6 +97,28 @@ struct CorrelateArgs {
 cudaError_t launch_correlate(const PlanDev& p, const CorrelateArgs& a, CorrConfig cfg,
                              cudaStream_t s);
 
+// Several segments of one length against the same templates (Sec. 3.2: a
+// template's transform serves a block of segments): per template the
+// forward transform runs once, then the product, inverse, sigma and tails
+// for each segment m < M into its own outputs.  F = 4096 (N >= 2^14) and
+// Lp <= 4096 only.
+constexpr int kMaxMulti = 8;
+struct MultiArgs {
+  const float* bank;
+  int64_t Lp;
+  int64_t k0, k1;
+  float kappa;
+  int M;
+  const float4* AB[kMaxMulti];
+  float* sigma[kMaxMulti];
+  bege_tail* recs[kMaxMulti];
+  uint64_t cap[kMaxMulti];
+  unsigned long long* counter[kMaxMulti];
+  float2* scratch;  // multi_scratch_bytes(): the template spectrum of each CTA
+};
+size_t multi_scratch_bytes(int sms);
+cudaError_t launch_correlate_multi(const PlanDev& p, const MultiArgs& a, cudaStream_t s);
+
 // Per-S launchers (one translation unit each); halfz: Lp <= F.
 cudaError_t launch_correlate_s1(const PlanDev& p, const CorrelateArgs& a, CorrConfig c, bool halfz,
                                 cudaStream_t s);
