@@ -31,7 +31,10 @@ Readings of the paper taken here (the paper is garbled or silent):
 * The forward transform uses e^{-i k t} (Eq. A2), the inverse e^{+...}/N.
 * The threshold is strict: |rho| > kappa sigma (Eq. tail writes ">").
 * The correlation is circular over all N lags (the template is zero-padded to
-  N, Sec. 3.2 step ii, and transformed with an N-point FFT).
+  N, Sec. 3.2 step ii, and transformed with an N-point FFT).  The optional
+  overlap-save form keeps the tails at the lags n <= N - L only, where the
+  circular sum equals the linear one (``correlate_linear``, ``tails_linear``);
+  sigma is unchanged.
 """
 from __future__ import annotations
 
@@ -219,6 +222,29 @@ def tails_band(rho: np.ndarray, sigma: float, kappa_lo: float, kappa_hi: float,
     out["lag"] = lags
     out["value"] = rho[lags]
     return out
+
+
+def correlate_linear(w: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Eq. A1 over the segment alone, without wrapping: rho[n] = sum_m w[m]
+    y[n + m] for the lags n = 0..N-L whose window y[n .. n+L-1] lies inside
+    the segment (the lags an overlap-save search keeps)."""
+    w = np.asarray(w, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n_valid = len(y) - len(w) + 1
+    out = np.zeros(max(n_valid, 0))
+    for m in range(len(w)):
+        out += w[m] * y[m:m + n_valid]
+    return out
+
+
+def tails_linear(rho: np.ndarray, sigma: float, kappa: float, length: int,
+                 k: int) -> np.ndarray:
+    """Eq. tail restricted to the lags n <= N - L of a length-L template
+    (overlap-save: only lags whose window does not wrap); sigma stays the
+    Parseval value over all N lags."""
+    rho = np.asarray(rho, dtype=np.float64)
+    keep = tails(rho, sigma, kappa, k)
+    return keep[keep["lag"] <= len(rho) - length]
 
 
 def search(y: np.ndarray, templates: np.ndarray, kappa: float, k0: int = 0,

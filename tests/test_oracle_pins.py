@@ -439,6 +439,54 @@ def test_tails_band_definition():
 
 
 # ----------------------------------------------------------------------------
+# Overlap-save lag mask (the circular correlation restricted to unwrapped lags)
+# ----------------------------------------------------------------------------
+def test_correlate_linear_is_numpy_valid_correlation():
+    """Eq. A1 without wrap is numpy's 'valid' cross-correlation, sum_m
+    y[n+m] w[m] for n = 0..N-L (a library special case)."""
+    g = rng(41)
+    y, w = g.standard_normal(300), g.standard_normal(37)
+    got = O.correlate_linear(w, y)
+    assert len(got) == 300 - 37 + 1
+    assert np.allclose(got, np.correlate(y, w, mode="valid"), rtol=0, atol=1e-12)
+
+
+def test_circular_equals_linear_on_unwrapped_lags_only():
+    """The FFT path's circular rho equals the linear correlation at the
+    lags n <= N - L, and differs at lags whose window wraps (there the sum
+    takes samples from the start of the segment)."""
+    g = rng(42)
+    n, length = 1024, 100
+    y, w = g.standard_normal(n), g.standard_normal(length)
+    circ = O.correlate_fft(w, y)
+    lin = O.correlate_linear(w, y)
+    assert np.allclose(circ[:n - length + 1], lin, rtol=0, atol=1e-10)
+    wrapped = circ[n - length + 1:]
+    direct = [sum(w[m] * y[(k + m) % n] for m in range(length)) for k in range(n - length + 1, n)]
+    assert np.allclose(wrapped, direct, atol=1e-10)
+    no_wrap = [sum(w[m] * y[k + m] for m in range(length) if k + m < n)
+               for k in range(n - length + 1, n)]
+    assert np.max(np.abs(np.asarray(no_wrap) - wrapped)) > 1e-3
+
+
+def test_tails_linear_is_the_unwrapped_part_of_the_tails():
+    """tails_linear keeps exactly the tails at lags n <= N - L, with the
+    same sigma; a tail at the last unwrapped lag N - L is kept and one at
+    N - L + 1 dropped."""
+    g = rng(43)
+    n, length = 512, 64
+    rho = g.standard_normal(n)
+    sigma = 0.5
+    rho[n - length] = 3.0
+    rho[n - length + 1] = -3.0
+    full = O.tails(rho, sigma, 4.0, 3)
+    lin = O.tails_linear(rho, sigma, 4.0, length, 3)
+    assert lin["lag"].tolist() == [int(x) for x in full["lag"] if x <= n - length]
+    assert n - length in lin["lag"].tolist() and n - length + 1 not in lin["lag"].tolist()
+    assert n - length + 1 in full["lag"].tolist()
+
+
+# ----------------------------------------------------------------------------
 # Two channels: simultaneous hits and Table 3 (Sec. 5)
 # ----------------------------------------------------------------------------
 def test_coincidences_worked_example():
