@@ -173,6 +173,29 @@ int bege_correlate_band(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t 
                         int64_t k_end, float kappa_lo, float kappa_hi, void* stream,
                         int32_t* job_id);
 
+/* Options of bege_correlate_ex; each field off (zero) gives bege_correlate. */
+typedef struct {
+  float kappa;     /* tails |rho_k[n]| > kappa sigma_k (Eq. tail), finite, >= 0 */
+  float kappa_hi;  /* 0 = no upper end; else also |rho_k[n]| < kappa_hi sigma_k (Sec. 5),
+                      finite and > kappa */
+  int32_t linear;  /* 1 = overlap-save: tails only at lags n <= N - L, where the
+                      length-L template window y[n .. n+L-1] does not wrap, so
+                      the circular correlation equals the linear one (Eq. A1 over
+                      the segment alone); sigma_k stays the Parseval value over
+                      all N lags.  0 = all N circular lags. */
+  int32_t project; /* 1 = also keep the per-lag maximum of bege_correlate_max, over
+                      the tails the other options keep */
+} bege_search_opts;
+
+/* The search with the tail epilogue's options combined: a band, the
+ * overlap-save lag mask and the per-lag maximum (host struct, read during
+ * the call only).  Records via bege_fetch_tails; a projection via
+ * bege_fetch_max.  Errors: as bege_correlate; EINVAL for an invalid field
+ * (linear and project must be 0 or 1). */
+int bege_correlate_ex(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                      int64_t k_end, const bege_search_opts* opts, void* stream,
+                      int32_t* job_id);
+
 /* Wait for a bege_correlate_max job and copy its projection to HOST arrays
  * of n = N entries: snr[n] = rho / sigma of the kept hit and tmpl[n] its
  * template index, or snr 0 and tmpl -1 where no template passes.

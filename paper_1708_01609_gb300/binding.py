@@ -64,6 +64,11 @@ class bege_serve_info(ctypes.Structure):
                 ("gpu_ms", ctypes.c_double)]
 
 
+class bege_search_opts(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_float), ("kappa_hi", ctypes.c_float),
+                ("linear", ctypes.c_int32), ("project", ctypes.c_int32)]
+
+
 class bege_tail(ctypes.Structure):
     _fields_ = [("tmpl", ctypes.c_uint32), ("lag", ctypes.c_uint32), ("value", ctypes.c_float)]
 
@@ -93,6 +98,8 @@ SIGNATURES = {
     "bege_fetch_max": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I64]),
     "bege_correlate_band": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64, ctypes.c_float,
                                            ctypes.c_float, _VP, _PI32]),
+    "bege_correlate_ex": (ctypes.c_int, [_VP, _I32, _I32, _I64, _I64,
+                                         ctypes.POINTER(bege_search_opts), _VP, _PI32]),
     "bege_fetch_tails": (ctypes.c_int, [_VP, _I32, _VP, _I64, _PI64, _PI64]),
     "bege_sort_tails": (ctypes.c_int, [_VP, _I64]),
     "bege_query": (ctypes.c_int, [_VP, _I32]),
@@ -260,6 +267,18 @@ class Context:
         jid = _I32()
         _check(self.lib.bege_correlate_band(self.h, seg, bank, k_begin, k_end, kappa_lo, kappa_hi,
                                             stream, ctypes.byref(jid)), "bege_correlate_band")
+        return jid.value
+
+    def bege_correlate_ex(self, seg: int, bank: int, k_begin: int, k_end: int, kappa: float,
+                          kappa_hi: float = 0.0, linear: bool = False, project: bool = False,
+                          stream: int = 0) -> int:
+        """The search with the epilogue options combined: band upper end
+        kappa_hi (0 = none), overlap-save lag mask (linear) and per-lag
+        maximum (project; fetch it with bege_fetch_max)."""
+        o = bege_search_opts(kappa, kappa_hi, int(linear), int(project))
+        jid = _I32()
+        _check(self.lib.bege_correlate_ex(self.h, seg, bank, k_begin, k_end, ctypes.byref(o),
+                                          stream, ctypes.byref(jid)), "bege_correlate_ex")
         return jid.value
 
     def bege_fetch_max(self, job: int, n: int):

@@ -666,7 +666,8 @@ int bege_define_bank_samples(bege_ctx* ctx, const float* samples, int64_t count,
 
 static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
                           int64_t k_end, float kappa, cudaStream_t s, float* dump_dev,
-                          int32_t* job_id, bool project = false, float kappa_hi = 0.f) {
+                          int32_t* job_id, bool project = false, float kappa_hi = 0.f,
+                          bool linear = false) {
   auto si = ctx->segs.find(seg_id);
   if (si == ctx->segs.end()) return fail(BEGE_EINVAL, "unknown segment handle");
   auto bi = ctx->banks.find(bank_id);
@@ -723,6 +724,9 @@ static int correlate_impl(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_
     a.status = reinterpret_cast<unsigned int*>(static_cast<char*>(job->buf->counter.ptr) + 8);
     a.proj = static_cast<unsigned long long*>(job->proj.ptr);
     a.kappa_hi = kappa_hi;
+    // overlap-save: the window y[n .. n+L-1] of a length-L template stays
+    // inside the segment for n <= N - L
+    if (linear) a.lag_end = (uint32_t)(seg->n - bank->L + 1);
     if (ctx->cfg.precision != 0) {
       e = bege::launch_correlate_tc(seg->plan->dev, a, ctx->cfg.precision, s);
     } else {
@@ -865,6 +869,24 @@ int bege_correlate_band(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t 
   std::lock_guard<std::mutex> lk(ctx->mu);
   return correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, kappa_lo,
                         static_cast<cudaStream_t>(stream), nullptr, job_id, false, kappa_hi);
+}
+
+int bege_correlate_ex(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                      int64_t k_end, const bege_search_opts* opts, void* stream,
+                      int32_t* job_id) {
+  if (!ctx || !opts || !job_id) return fail(BEGE_EINVAL, "NULL argument");
+  const bege_search_opts o = *opts;
+  if (!std::isfinite(o.kappa) || !std::isfinite(o.kappa_hi))
+    return fail(BEGE_EINVAL, "kappa and kappa_hi must be finite");
+  if (o.kappa_hi != 0.f && !(o.kappa_hi > o.kappa))
+    return fail(BEGE_EINVAL, "kappa_hi must be 0 (no upper end) or above kappa");
+  if ((o.linear != 0 && o.linear != 1) || (o.project != 0 && o.project != 1))
+    return fail(BEGE_EINVAL, "linear and project must be 0 or 1");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return correlate_impl(ctx, seg_id, bank_id, k_begin, k_end, o.kappa,
+                        static_cast<cudaStream_t>(stream), nullptr, job_id, o.project == 1,
+                        o.kappa_hi, o.linear == 1);
 }
 
 int bege_fetch_max(bege_ctx* ctx, int32_t job_id, float* snr, int32_t* tmpl, int64_t n) {

@@ -567,12 +567,15 @@ struct TailOut {
   // optional upper end of a tail band (Sec. 5): keep |rho| < kappa_hi sigma
   // as well; 0 = no upper end
   float kappa_hi = 0.f;
+  // optional overlap-save mask: tails only at lags n < lag_end (the lags
+  // whose template window does not wrap); all N lags by default
+  uint32_t lag_end = 0xffffffffu;
 };
 
-// EXT: the extended epilogue, the per-lag maximum a.proj and the band's
-// upper end a.kappa_hi (compiled only into the kernels that serve
-// bege_correlate_max and bege_correlate_band, so the others keep their code
-// unchanged).  sigma: the template's sigma (thr = kappa sigma).
+// EXT: the extended epilogue, the per-lag maximum a.proj, the band's upper
+// end a.kappa_hi and the lag mask a.lag_end (compiled only into the kernels
+// that serve bege_correlate_max, bege_correlate_band and bege_correlate_ex,
+// so the others keep their code unchanged).  sigma: the template's sigma (thr = kappa sigma).
 template <int F, int S, int NC, int T, bool EXT = false>
 __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, int rank, float thr,
                                                  uint32_t tmpl, int64_t krow, const TailOut& a,
@@ -609,8 +612,9 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
       for (int n2 = 0; n2 < S; ++n2) {
         if constexpr (EXT) {
           const float ax = fabsf(t[n2].x), ay = fabsf(t[n2].y);
-          mask |= (ax > thrH && ax < hiH ? 1u : 0u) << (2 * n2);
-          mask |= (ay > thrH && ay < hiH ? 1u : 0u) << (2 * n2 + 1);
+          const uint32_t lag = (uint32_t)(2 * (n1 + F * n2));
+          mask |= (ax > thrH && ax < hiH && lag < a.lag_end ? 1u : 0u) << (2 * n2);
+          mask |= (ay > thrH && ay < hiH && lag + 1u < a.lag_end ? 1u : 0u) << (2 * n2 + 1);
         } else {
           mask |= (fabsf(t[n2].x) > thrH ? 1u : 0u) << (2 * n2);
           mask |= (fabsf(t[n2].y) > thrH ? 1u : 0u) << (2 * n2 + 1);
@@ -758,7 +762,7 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
   const int ncl = gridDim.x / C;
   const int nz = (int)(a.Lp / 2);
   const int nfold = (nz + F - 1) / F;
-  const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj, a.kappa_hi};
+  const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj, a.kappa_hi, a.lag_end};
 
   for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
     template_columns<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold, a.AB);
@@ -816,12 +820,13 @@ static cudaError_t launch_corr_tp(const PlanDev& p, const CorrelateArgs& a, cuda
   return cudaLaunchKernelEx(&cfg, kern, p, a);
 }
 
-// The extended epilogue (bege_correlate_max, bege_correlate_band) runs in
-// its own instantiation.
+// The extended epilogue (bege_correlate_max, bege_correlate_band,
+// bege_correlate_ex) runs in its own instantiation.
 template <int F, int S, int NC, int T, int MINB, bool HALFZ>
 static cudaError_t launch_corr_t(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
-  return (a.proj || a.kappa_hi > 0.f) ? launch_corr_tp<F, S, NC, T, MINB, HALFZ, true>(p, a, s)
-                                      : launch_corr_tp<F, S, NC, T, MINB, HALFZ, false>(p, a, s);
+  const bool ext = a.proj || a.kappa_hi > 0.f || a.lag_end < (uint32_t)p.g.N;
+  return ext ? launch_corr_tp<F, S, NC, T, MINB, HALFZ, true>(p, a, s)
+             : launch_corr_tp<F, S, NC, T, MINB, HALFZ, false>(p, a, s);
 }
 
 template <int F, int S, int NC, int T>

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
   const int cid = blockIdx.x / C;
   const int ncl = gridDim.x / C;
   const int nz = (int)(a.Lp / 2);
-  const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj, a.kappa_hi};
+  const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj, a.kappa_hi, a.lag_end};
   uint32_t parity = 0;
   bool ok = true;
   const int warp = tid >> 5, lane = tid & 31;

@@ -93,6 +93,7 @@ struct CorrelateArgs {
   unsigned int* status;  // optional: set non-zero by a kernel whose bounded wait gave up
   unsigned long long* proj = nullptr;  // optional: per-lag maximum over the bank (Eq. Ak)
   float kappa_hi = 0.f;                // optional: tails only below kappa_hi sigma (0 = none)
+  uint32_t lag_end = 0xffffffffu;      // optional: tails only at lags < lag_end (overlap-save)
 };
 cudaError_t launch_correlate(const PlanDev& p, const CorrelateArgs& a, CorrConfig cfg,
                              cudaStream_t s);

@@ -149,6 +149,101 @@ def test_band_tails_match_oracle(prec):
     assert n_ref > 300  # ~470 expected from noise alone, plus the injection
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_linear_tails_match_oracle(prec):
+    """Overlap-save mask: tails only at lags n <= N - L (the windows that do
+    not wrap), on the N = 2^14 case against the oracle's tails_linear; sigma
+    is the full Parseval value."""
+    seg_data, params = S.small_case()
+    kappa, length, n = 4.0, 4096, len(seg_data.y)
+    ctx = make_ctx(tail_capacity=1 << 20, precision=prec)
+    seg = ctx.bege_load_segment(seg_data.y)
+    bid = ctx.bege_define_bank(params)
+    job = ctx.bege_correlate_ex(seg, bid, 0, len(params), kappa, linear=True)
+    recs, total = ctx.bege_fetch_tails(job)
+    sg = ctx.bege_get_sigma(job, len(params))
+    full = ctx.bege_correlate(seg, bid, 0, len(params), kappa)
+    r_full, _ = ctx.bege_fetch_tails(full)
+    ctx.close()
+    assert total == len(recs)
+    assert np.all(recs["lag"] <= n - length)
+    assert np.sum(r_full["lag"] > n - length) > 0  # the mask removes something here
+    bank = O.chirp_bank(params, 4096.0, 4096, 0.05)
+    rho, sig = oracle_rho(seg_data.y, bank)
+    tol = 1e-5 if prec == 0 else 2e-3
+    assert np.max(np.abs(sg / sig - 1)) <= (1e-6 if prec == 0 else 1e-3)
+    near = max(1e-3, tol)
+    got = {(int(t), int(l)): float(v) for t, l, v in zip(recs["tmpl"], recs["lag"], recs["value"])}
+    n_ref = 0
+    for k in range(len(params)):
+        ref = O.tails_linear(rho[k], sig[k], kappa, length, k)
+        lin = O.correlate_linear(bank[k], seg_data.y)
+        assert np.allclose(rho[k][:n - length + 1], lin, atol=1e-9)
+        for lag, v in zip(ref["lag"], ref["value"]):
+            if (k, int(lag)) not in got:
+                assert abs(abs(v) / sig[k] - kappa) <= near, (k, lag)
+                continue
+            n_ref += 1
+            assert abs(got[(k, int(lag))] - v) <= tol * sig[k]
+    for (k, lag), v in got.items():
+        assert abs(rho[k][lag]) / sig[k] >= kappa - near
+    assert n_ref > 100
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_ex_options_compose(prec):
+    """bege_correlate_ex with band, mask and projection together: the
+    records are the plain search's records filtered by both rules, and the
+    projection is the per-lag maximum of those records."""
+    seg_data, params = S.small_case()
+    lo, hi, length, n = 3.5, 6.0, 4096, len(seg_data.y)
+    ctx = make_ctx(tail_capacity=1 << 20, precision=prec)
+    seg = ctx.bege_load_segment(seg_data.y)
+    bid = ctx.bege_define_bank(params)
+    plain = ctx.bege_correlate(seg, bid, 0, len(params), lo)
+    r_plain, _ = ctx.bege_fetch_tails(plain, sort=True)
+    sig = ctx.bege_get_sigma(plain, len(params))
+    job = ctx.bege_correlate_ex(seg, bid, 0, len(params), lo, kappa_hi=hi, linear=True,
+                                project=True)
+    recs, total = ctx.bege_fetch_tails(job, sort=True)
+    snr, tmpl = ctx.bege_fetch_max(job, n)
+    assert np.array_equal(ctx.bege_get_sigma(job, len(params)), sig)
+    ctx.close()
+    assert total == len(recs)
+    s32 = sig.astype(np.float32)[r_plain["tmpl"]]
+    keep = (np.abs(r_plain["value"]) < np.float32(hi) * s32) & (r_plain["lag"] <= n - length)
+    want = r_plain[keep]
+    # the same FP32 values: bitwise equal except where |rho| meets hi sigma in the last bit
+    edge = np.abs(np.abs(want["value"]) / s32[keep] - hi) <= 1e-6
+    key = lambda r: set(zip(r["tmpl"].tolist(), r["lag"].tolist()))
+    assert key(want[~edge]) <= key(recs) <= key(want)
+    common = np.isin(want["tmpl"].astype(np.int64) << 32 | want["lag"],
+                     recs["tmpl"].astype(np.int64) << 32 | recs["lag"])
+    assert np.array_equal(want[common], recs)
+    ps, pk = projection_of_records(recs, sig, lo, n)
+    assert np.array_equal(ps, snr) and np.array_equal(pk, tmpl)
+    assert np.all(tmpl[n - length + 1:] == -1) and np.any(tmpl >= 0)
+
+
+def test_ex_rejects_bad_options():
+    from paper_1708_01609_gb300.binding import BegeError
+    seg_data, params = S.small_case()
+    ctx = make_ctx(tail_capacity=1 << 16)
+    seg = ctx.bege_load_segment(seg_data.y)
+    bid = ctx.bege_define_bank(params)
+    for kw in ({"kappa": 5.0, "kappa_hi": 4.0}, {"kappa": 5.0, "kappa_hi": 5.0},
+               {"kappa": float("nan")}, {"kappa": -1.0}, {"kappa": 5.0, "kappa_hi": float("inf")}):
+        with pytest.raises(BegeError):
+            ctx.bege_correlate_ex(seg, bid, 0, len(params), **kw)
+    import ctypes
+    from paper_1708_01609_gb300.binding import bege_search_opts
+    o = bege_search_opts(5.0, 0.0, 2, 0)
+    jid = ctypes.c_int32()
+    assert ctx.lib.bege_correlate_ex(ctx.h, seg, bid, 0, len(params), ctypes.byref(o), None,
+                                     ctypes.byref(jid)) != 0
+    ctx.close()
+
+
 def test_two_channel_coincidences():
     """Two detector channels (independent band-limited noise) with the same
     chirp injected at the same offset, each projected on the GPU: the
