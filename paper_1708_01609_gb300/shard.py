@@ -1,4 +1,5 @@
-"""Multi-rank host logic: bank shards, tail gathering, failed-rank re-queue.
+"""Multi-rank host logic: bank shards, tail gathering, per-lag maxima
+merged across shards, failed-rank re-queue.
 
 Every (segment, template) correlation is independent (the paper's partition
 of the bank into groups W_alpha and the data into blocks Y_beta, Sec. 3.1),
@@ -33,6 +34,54 @@ def merge_tails(parts: list[np.ndarray]) -> np.ndarray:
         return np.empty(0, dtype=[("tmpl", np.uint32), ("lag", np.uint32), ("value", np.float32)])
     t = np.concatenate(parts)
     return np.sort(t, order=["tmpl", "lag"])
+
+
+def projection_key(snr: np.ndarray, tmpl: np.ndarray) -> np.ndarray:
+    """Per-lag maximum (Eq. Ak over a shard of the bank) as one int64 key
+    per lag, the device's ordering: (FP32 bits of rho/sigma) << 32 |
+    ~template, 0 where no template hit.  The kept values are above kappa > 0,
+    so their bits order like the values and stay below 2^63; equal values
+    keep the smaller template."""
+    snr = np.asarray(snr, dtype=np.float32)
+    tmpl = np.asarray(tmpl, dtype=np.int32)
+    hit = tmpl >= 0
+    if np.any(snr[hit] <= 0):
+        raise ValueError("a kept per-lag maximum must be positive")
+    bits = snr.view(np.uint32).astype(np.int64)
+    low = (~tmpl.astype(np.uint32)).astype(np.int64)
+    return np.where(hit, (bits << 32) | low, 0)
+
+
+def projection_from_key(key: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Inverse of projection_key: (snr FP32, template int32, -1 = no hit)."""
+    key = np.asarray(key, dtype=np.int64)
+    snr = (key >> 32).astype(np.uint32).view(np.float32).copy()
+    tmpl = (~(key & 0xFFFFFFFF).astype(np.uint32)).astype(np.int32)
+    none = key == 0
+    snr[none], tmpl[none] = 0.0, -1
+    return snr, tmpl
+
+
+def merge_projections(parts: list[tuple[np.ndarray, np.ndarray]]):
+    """Element-wise maximum of per-shard projections of one segment's N
+    lags (the one exchange the per-lag maximum needs when the bank is
+    split): the largest rho/sigma per lag over all shards, ties to the
+    smaller template."""
+    if not parts:
+        raise ValueError("no projections to merge")
+    key = projection_key(*parts[0])
+    for p in parts[1:]:
+        key = np.maximum(key, projection_key(*p))
+    return projection_from_key(key)
+
+
+def all_reduce_projection(dist, snr: np.ndarray, tmpl: np.ndarray):
+    """merge_projections across the ranks of ``dist``: one all_reduce(MAX)
+    of the N int64 keys in host memory (gloo), the result on every rank."""
+    import torch
+    key = torch.from_numpy(projection_key(snr, tmpl))
+    dist.all_reduce(key, op=dist.ReduceOp.MAX)
+    return projection_from_key(key.numpy())
 
 
 def run_sharded(dist, compute, count: int, chunk: int, fail_rank: int | None = None,

@@ -79,3 +79,51 @@ def test_shard_ranges_cover_bank():
             assert all(a[1] == b[0] for a, b in zip(r, r[1:]))
             sizes = [b - a for a, b in r]
             assert max(sizes) - min(sizes) <= 1
+
+
+def projection_worker(rank, world, port, out_dir):
+    """Each rank projects its own shard of the bank (the oracle's per-lag
+    maximum, Eq. Ak over rows [k0, k1)); the shards meet in one host
+    all_reduce(MAX) of the packed keys."""
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    y, bank, O = small_problem()
+    k0, k1 = shard.shard_ranges(len(bank), world)[rank]
+    rho = np.stack([O.correlate_fft(w, y) for w in bank[k0:k1]])
+    sig = np.array([O.sigma_rms(r) for r in rho])
+    snr, tmpl = O.max_projection(rho, sig, 2.5, k0=k0)
+    m_snr, m_tmpl = shard.all_reduce_projection(dist, snr, tmpl)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "proj.npy"), np.stack([m_snr, m_tmpl.astype(np.float32)]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_merge_projections(tmp_path):
+    world = 2
+    mp.start_processes(projection_worker, args=(world, free_port(), str(tmp_path)),
+                       nprocs=world, start_method="spawn")
+    m_snr, m_tmpl = np.load(tmp_path / "proj.npy")
+    y, bank, O = small_problem()
+    rho = np.stack([O.correlate_fft(w, y) for w in bank])
+    sig = np.array([O.sigma_rms(r) for r in rho])
+    snr, tmpl = O.max_projection(rho, sig, 2.5)
+    assert np.sum(tmpl >= 0) > 20 and len(np.unique(tmpl[tmpl >= 0])) > 1
+    assert np.array_equal(m_tmpl.astype(np.int32), tmpl)
+    assert np.array_equal(m_snr, snr.astype(np.float32))
+
+
+def test_merge_projections_keeps_max_and_smaller_template_on_ties():
+    a_snr = np.array([0.0, 5.0, 6.0, 7.0], np.float32)
+    a_tm = np.array([-1, 3, 4, 9], np.int32)
+    b_snr = np.array([5.5, 0.0, 6.5, 7.0], np.float32)
+    b_tm = np.array([12, -1, 20, 2], np.int32)
+    snr, tm = shard.merge_projections([(a_snr, a_tm), (b_snr, b_tm)])
+    assert snr.tolist() == [5.5, 5.0, 6.5, 7.0]
+    assert tm.tolist() == [12, 3, 20, 2]
+    s1, t1 = shard.merge_projections([(a_snr, a_tm)])
+    assert np.array_equal(s1, a_snr) and np.array_equal(t1, a_tm)
+    with pytest.raises(ValueError):
+        shard.merge_projections([(np.array([-1.0], np.float32), np.array([0], np.int32))])
