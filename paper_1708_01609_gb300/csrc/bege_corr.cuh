@@ -69,7 +69,8 @@ struct Lay {
   static constexpr size_t colptr = ws + align16(16 * 8);
   static constexpr size_t red = colptr + align16(16 * 8);
   static constexpr size_t sigpart = red + align16(32 * 4);
-  static constexpr size_t total = sigpart + align16(4);
+  static constexpr size_t sigall = sigpart + align16(4);
+  static constexpr size_t total = sigall + align16(16 * 4);
 };
 
 extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -88,6 +89,7 @@ struct Smem {
   static __device__ __forceinline__ float2** colptr() { return reinterpret_cast<float2**>(smem_raw + L::colptr); }
   static __device__ __forceinline__ float* red() { return reinterpret_cast<float*>(smem_raw + L::red); }
   static __device__ __forceinline__ float* sigpart() { return reinterpret_cast<float*>(smem_raw + L::sigpart); }
+  static __device__ __forceinline__ float* sigall() { return reinterpret_cast<float*>(smem_raw + L::sigall); }
 };
 
 // Column ownership for S >= 2 columns split over S/NC CTAs, S given at run
@@ -661,10 +663,29 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
   }
 }
 
+// The CTA's share of sum |Y|^2: in its sigpart slot, and with SIGPUSH also
+// in slot grank of every CTA's sigall array.
+template <int F, int S, int NC, bool SIGPUSH>
+__device__ __forceinline__ void store_sigma_partial(int grank, float s) {
+  using SM = Smem<F, NC>;
+  *SM::sigpart() = s;
+  if constexpr (SIGPUSH) {
+    constexpr int C = ColMap<S, NC>::C;
+    cg::cluster_group cluster = cg::this_cluster();
+#pragma unroll
+    for (int q = 0; q < C; ++q) *cluster.map_shared_rank(SM::sigall() + grank, (unsigned)q) = s;
+  }
+}
+
 // S2-S5 for one template on this CTA's columns; leaves the CTA's share of
 // sum |Y|^2 in its sigpart slot and T_b in its columns (the caller
 // synchronises the cluster before the combine).
-template <int F, int S, int NC, int T, bool HALFZ>
+//
+// SIGPUSH: the CTA's partial is also stored into slot grank of every CTA's
+// sigall array, so each CTA sums the cluster's partials from its own memory
+// after the next cluster barrier (slot q is rewritten only after the
+// barrier that follows every CTA's read of it).
+template <int F, int S, int NC, int T, bool HALFZ, bool SIGPUSH = false>
 __device__ __forceinline__ void template_columns(int grank, const float* __restrict__ src, int nz,
                                                  int nfold, const float4* __restrict__ AB,
                                                  int s_rt = S) {
@@ -680,7 +701,7 @@ __device__ __forceinline__ void template_columns(int grank, const float* __restr
     if (threadIdx.x == 0) {
       float s = 0.f;
       for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
-      *SM::sigpart() = s;
+      store_sigma_partial<F, S, NC, SIGPUSH>(grank, s);
     }
     __syncthreads();
     stockham_pass<F, NC, T, 16, 16, true>(SM::cols(), SM::tw2());
@@ -720,7 +741,7 @@ __device__ __forceinline__ void template_columns(int grank, const float* __restr
     if (threadIdx.x == 0) {
       float s = 0.f;
       for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
-      *SM::sigpart() = s;
+      store_sigma_partial<F, S, NC, SIGPUSH>(grank, s);
     }
     // S5: inverse column FFTs (the first pass reads after the barrier above)
     inverse_columns<F, S, NC, T>();
@@ -748,6 +769,17 @@ __device__ __forceinline__ float group_sigma(float* sigpart, int gbase, int N) {
   return sqrtf(2.0f * tot) / (float)N;
 }
 
+// A cluster barrier that orders only earlier reads of distributed shared
+// memory before later writes (the combine's remote reads before the next
+// template overwrites the columns): every remote value has fed a warp vote
+// or the threshold before its thread arrives, so the reads have completed
+// and the arrive needs no release fence.  Data that other CTAs read later
+// is published by the full (release / acquire) barrier before the combine.
+__device__ __forceinline__ void cluster_sync_after_reads() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" :::
+               "memory");
+}
+
 template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool EXT>
 __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, CorrelateArgs a) {
   constexpr int C = ColMap<S, NC>::C;
@@ -765,15 +797,21 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
   const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj, a.kappa_hi, a.lag_end};
 
   for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
-    template_columns<F, S, NC, T, HALFZ>(rank, a.bank + k * a.Lp, nz, nfold, a.AB);
+    template_columns<F, S, NC, T, HALFZ, true>(rank, a.bank + k * a.Lp, nz, nfold, a.AB);
     cluster.sync();  // every column and every sigma partial of the cluster is ready
-    const float sigma = group_sigma<S, NC>(Smem<F, NC>::sigpart(), 0, N);
+    float sigma;
+    {  // Eq. PT over the cluster's partials, summed in rank order as group_sigma does
+      float tot = 0.f;
+#pragma unroll
+      for (int q = 0; q < C; ++q) tot += Smem<F, NC>::sigall()[q];
+      sigma = sqrtf(2.0f * tot) / (float)N;
+    }
     const int64_t krow = k - a.k0;
     if (rank == 0 && threadIdx.x == 0) a.sigma[krow] = sigma;
     // S6: S-point combine, threshold, warp-ballot compaction
     combine_and_emit<F, S, NC, T, EXT>(Smem<F, NC>::colptr(), H, rank, a.kappa * sigma,
                                        (uint32_t)k, krow, out, sigma);
-    cluster.sync();  // remote reads done before the columns are overwritten
+    cluster_sync_after_reads();  // remote reads done before the columns are overwritten
   }
 }
 

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kT, kMinB) correlate_multi_kernel(PlanDev p, M
       const TailOut out{a.recs[m], a.cap[m], a.counter[m], nullptr};
       combine_and_emit<kF, S, kNC, kT>(SM::colptr(), H, rank, a.kappa * sigma, (uint32_t)k, krow,
                                        out, sigma);
-      cluster.sync();  // remote reads done before the columns are overwritten
+      cluster_sync_after_reads();  // remote reads done before the columns are overwritten
     }
   }
 }

@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
       if (rank == 0 && tid == 0) a.sigma[krow] = sigma;
       combine_and_emit<kF, S, NC, T, true>(SM::colptr(), H, rank, a.kappa * sigma, (uint32_t)k,
                                            krow, out, sigma);
-      cluster.sync();  // remote reads done before the regions are overwritten
+      cluster_sync_after_reads();  // remote reads done before the regions are overwritten
     }
   }
 
