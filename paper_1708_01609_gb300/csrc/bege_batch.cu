@@ -70,7 +70,8 @@ __device__ __forceinline__ void run_item(const BatchArgs& b, const ItemState* st
         default: combine_and_emit<kF, 16, kNC, kT>(cp, S * 4096, grank, thr, (uint32_t)k, krow, out, 0.f); break;
       }
     }
-    if (C == 1) __syncthreads(); else cluster.sync();
+    // remote reads done before the columns are overwritten
+    if (C == 1) __syncthreads(); else cluster_sync_after_reads();
   }
 }
 

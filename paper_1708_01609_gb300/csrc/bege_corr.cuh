@@ -248,7 +248,7 @@ __device__ __forceinline__ void fwd_first_pass(int rank, const float* __restrict
 // Last inverse pass (radix 16, Ns = F/16) fused with the output twiddle
 // T_b[n1] = wH^(-b n1) x[n1], n1 = k + r F/16, factored as
 // conj(wH^(b k)) * w(16 S)^(-b r).
-template <int F, int S, int NC, int T>
+template <int F, int S, int NC, int T, bool TRAIL = true>
 __device__ __forceinline__ void inv_last_pass() {
   using SM = Smem<F, NC>;
   constexpr int NB = F / 16;
@@ -284,7 +284,7 @@ __device__ __forceinline__ void inv_last_pass() {
       for (int r = 0; r < 16; ++r) col[r * step] = v[r];
     }
   }
-  __syncthreads();
+  if constexpr (TRAIL) __syncthreads();
 }
 
 template <int F, int S, int NC, int T, bool HALFZ>
@@ -704,8 +704,11 @@ __device__ __forceinline__ void template_columns(int grank, const float* __restr
       store_sigma_partial<F, S, NC, SIGPUSH>(grank, s);
     }
     __syncthreads();
-    stockham_pass<F, NC, T, 16, 16, true>(SM::cols(), SM::tw2());
-    inv_last_pass<F, S, NC, T>();
+    // rounds of these two passes touch disjoint columns, so (with two or
+    // more rounds) a later round's barrier orders the first pass's stores
+    // before the second pass's loads
+    stockham_pass<F, NC, T, 16, 16, true, false>(SM::cols(), SM::tw2());
+    inv_last_pass<F, S, NC, T, !SIGPUSH>();  // without it, a cluster barrier follows
   } else {
     // S2: template spectrum (column FFTs of the packed, twiddled template)
     forward_columns<F, S, NC, T, HALFZ>(grank, src, nz, nfold);

@@ -145,7 +145,7 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
 // costs fewer barriers but spills at 128 registers and measured slower.
 // With F/R and NS multiples of 16 the padded addresses of a butterfly are
 // one base plus constants.
-template <int F, int NC, int T, int R, int NS, bool INV>
+template <int F, int NC, int T, int R, int NS, bool INV, bool TRAIL = true>
 __device__ __forceinline__ void stockham_pass(float2* cols, const float2* tw) {
   constexpr int NB = F / R;
   static_assert(T % NB == 0, "rounds must cover whole columns");
@@ -194,7 +194,11 @@ __device__ __forceinline__ void stockham_pass(float2* cols, const float2* tw) {
       }
     }
   }
-  __syncthreads();
+  // TRAIL = false: the caller's next pass runs the same rounds over the same
+  // columns, so with two or more rounds each column's stores here and its
+  // loads there are separated by a later round's barrier (of this pass or
+  // of the next); with one round they are not, and the barrier stays
+  if constexpr (TRAIL || rounds < 2) __syncthreads();
 }
 
 }  // namespace bege
