@@ -236,18 +236,32 @@ def correlate_source_hash() -> str:
     return h.hexdigest()
 
 
-def traffic_record(templates: int):
-    """DRAM bytes per correlate launch from the committed ncu summary, if the
-    kernel source is unchanged since it was captured; else None."""
+def _counter_record():
+    """The committed ncu record of the correlate kernel, if its source is
+    unchanged since the capture; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get("correlate_kernel")
-    if not rec:
+    if not rec or rec.get("source_sha256") != correlate_source_hash():
         return None
-    if rec.get("source_sha256") != correlate_source_hash():
+    return rec
+
+
+def traffic_record(templates: int):
+    """DRAM bytes per correlate launch from the committed ncu summary, if the
+    kernel source is unchanged since it was captured; else None."""
+    rec = _counter_record()
+    return None if rec is None else rec["dram_bytes_per_correlation"] * templates
+
+
+def ncu_counters():
+    """Pipe and issue utilisation of the correlate kernel from the same ncu
+    capture (percent of peak), or None when the source has changed."""
+    rec = _counter_record()
+    if rec is None or "counters" not in rec:
         return None
-    return rec["dram_bytes_per_correlation"] * templates
+    return dict(rec["counters"], source="profiles/traffic.json")
 
 
 def run_ours(args):
@@ -356,6 +370,7 @@ def run_ours(args):
             "peak_basis": (f"FP32 ALU: {props.multi_processor_count} SMs x 128 lanes x 2 flops x "
                            f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)"),
             "flop_convention": "5 N log2 N per correlation (Eq. nd)",
+            "ncu": ncu_counters(),
         },
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": N_SAMPLES * 4,
                 "d2h_bytes_per_step": int(8 + 12 * statistics.mean(tails_e2e))},
