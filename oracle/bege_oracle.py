@@ -357,9 +357,3 @@ def table3_rows_two(snr1, tmpl1, snr2, tmpl2, f0) -> np.ndarray:
     return np.array(rows, dtype=[("offset", np.int64), ("rho1000_1", np.int32),
                                  ("rho1000_2", np.int32), ("f0_1", np.int32),
                                  ("f0_2", np.int32)])
-
-
-def near_threshold(values: np.ndarray, sigma: np.ndarray, kappa: float,
-                   band: float = 1e-3) -> np.ndarray:
-    """True where ||rho| - kappa sigma| <= band * sigma (excluded from set parity)."""
-    return np.abs(np.abs(values) - kappa * sigma) <= band * sigma
