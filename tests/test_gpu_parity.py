@@ -49,6 +49,9 @@ DUMP_CASES = [
     (1 << 10, 1024), (1 << 10, 301), (1 << 11, 1000), (1 << 12, 4096), (1 << 13, 4096),
     (1 << 14, 4096), (1 << 14, 16384), (1 << 14, 7), (1 << 15, 4096), (1 << 15, 9999),
     (1 << 16, 4096), (1 << 16, 65536), (1 << 17, 4096), (1 << 17, 8191),
+    # degenerate and maximum lengths: a one-sample template (rho = w0 y), and
+    # the longest template in the longest segment (the folded first pass)
+    (1 << 12, 1), (1 << 16, 1), (1 << 17, 65536),
 ]
 
 
