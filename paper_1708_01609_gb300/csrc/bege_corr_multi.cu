@@ -44,13 +44,18 @@ __global__ void __launch_bounds__(kT, kMinB) correlate_multi_kernel(PlanDev p, M
       if (threadIdx.x == 0) {
         float s = 0.f;
         for (int w = 0; w < kT / 32; ++w) s += SM::red()[w];
-        *SM::sigpart() = s;
+        store_sigma_partial<kF, S, kNC, true>(rank, s);
       }
       __syncthreads();
-      stockham_pass<kF, kNC, kT, 16, 16, true>(SM::cols(), SM::tw2());
-      inv_last_pass<kF, S, kNC, kT>();
+      // two rounds per pass over disjoint columns: the last inverse pass's
+      // round barriers order these stores; a cluster barrier follows it
+      stockham_pass<kF, kNC, kT, 16, 16, true, false>(SM::cols(), SM::tw2());
+      inv_last_pass<kF, S, kNC, kT, false>();
       cluster.sync();  // every column and sigma partial of the cluster is ready
-      const float sigma = group_sigma<S, kNC>(SM::sigpart(), 0, N);
+      float tot = 0.f;  // Eq. PT over the cluster's partials, in rank order
+#pragma unroll
+      for (int q = 0; q < C; ++q) tot += SM::sigall()[q];
+      const float sigma = sqrtf(2.0f * tot) / (float)N;
       if (rank == 0 && threadIdx.x == 0) a.sigma[m][krow] = sigma;
       const TailOut out{a.recs[m], a.cap[m], a.counter[m], nullptr};
       combine_and_emit<kF, S, kNC, kT>(SM::colptr(), H, rank, a.kappa * sigma, (uint32_t)k, krow,
