@@ -92,3 +92,42 @@ def test_sort_tails_orders_by_template_then_lag():
     lib = binding.load_library()
     assert lib.bege_sort_tails(None, 5) == binding.BEGE_EINVAL
     assert lib.bege_sort_tails(None, -1) == binding.BEGE_EINVAL
+
+
+STRUCTS = ["bege_config", "bege_chirp", "bege_tail", "bege_search_opts", "bege_batch_entry",
+           "bege_serve_config", "bege_serve_info"]
+
+
+def test_header_is_c_and_binding_layouts_match(tmp_path):
+    """The header compiles as plain C11 (gcc, -Wall -Werror), and every
+    struct's size and field offsets in C equal the ctypes binding's."""
+    import shutil
+    import subprocess
+    from paper_1708_01609_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bege.h"', "int main(void) {"]
+    for name in STRUCTS:
+        st = getattr(binding, name)
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for line in out.splitlines():
+        name, key, value = line.split()
+        got[(name, key)] = int(value)
+    for name in STRUCTS:
+        st = getattr(binding, name)
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert got[(name, field)] == getattr(st, field).offset, (name, field)
