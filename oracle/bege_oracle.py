@@ -310,12 +310,14 @@ def max_projection(rho: np.ndarray, sigma: np.ndarray, kappa: float, k0: int = 0
 def table3_rows(snr: np.ndarray, tmpl: np.ndarray, f0: np.ndarray) -> np.ndarray:
     """Table 3's encoding of a projection: one row per lag with a hit, the
     sample offset (1-based, as the table counts), 1000 x snr as an integer
-    and the hit template's initial frequency f0 [Hz] as an integer."""
+    and the hit template's initial frequency f0 [Hz] as an integer.  Both
+    integers round the exact value toward zero: the product is taken in
+    FP64, which is exact for FP32 inputs."""
     lags = np.nonzero(tmpl >= 0)[0]
     rows = np.empty(len(lags), dtype=[("offset", np.int64), ("rho1000", np.int32),
                                        ("f0", np.int32)])
     rows["offset"] = lags + 1
-    rows["rho1000"] = np.floor(1000.0 * snr[lags]).astype(np.int32)
+    rows["rho1000"] = np.floor(1000.0 * np.asarray(snr, dtype=np.float64)[lags]).astype(np.int32)
     rows["f0"] = np.floor(np.asarray(f0)[tmpl[lags]]).astype(np.int32)
     return rows
 
