@@ -30,6 +30,14 @@
 
 #include <stdint.h>
 
+/* The library is built with hidden symbol visibility; only the calls
+ * declared here are exported. */
+#if defined(__GNUC__)
+#define BEGE_API __attribute__((visibility("default")))
+#else
+#define BEGE_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -74,10 +82,10 @@ typedef struct {
 /* Create a context on CUDA device `device`.  `cfg` may be NULL for defaults
  * (fs = 4096, no budget, 1<<20 tail records, FP32).  *out receives the
  * context; destroy it with bege_destroy.  Errors: EINVAL (bad cfg), ECUDA. */
-int bege_create(bege_ctx** out, int device, const bege_config* cfg);
+BEGE_API int bege_create(bege_ctx** out, int device, const bege_config* cfg);
 
 /* Free every device buffer and handle of the context. */
-int bege_destroy(bege_ctx* ctx);
+BEGE_API int bege_destroy(bege_ctx* ctx);
 
 /* Segment spectrum (Eq. 3S first step; Sec. 3.2 step i).  Copies `n` FP32
  * strain samples from HOST memory `strain`, computes the unnormalised DFT
@@ -86,13 +94,13 @@ int bege_destroy(bege_ctx* ctx);
  * `channel` is a caller label (e.g. 0 = H1, 1 = L1) stored with the segment.
  * *seg_id receives the handle.  Errors: EINVAL (n not a power of two in
  * range, NULL pointers), EBUDGET, ENOMEM, ECUDA. */
-int bege_load_segment(bege_ctx* ctx, const float* strain, int64_t n, int32_t channel,
-                      void* stream, int32_t* seg_id);
+BEGE_API int bege_load_segment(bege_ctx* ctx, const float* strain, int64_t n, int32_t channel,
+                               void* stream, int32_t* seg_id);
 
 /* As bege_load_segment, but `strain_dev` is a DEVICE pointer to n FP32
  * samples on the context's GPU (read on `stream`; not retained). */
-int bege_load_segment_device(bege_ctx* ctx, const float* strain_dev, int64_t n,
-                             int32_t channel, void* stream, int32_t* seg_id);
+BEGE_API int bege_load_segment_device(bege_ctx* ctx, const float* strain_dev, int64_t n,
+                                      int32_t channel, void* stream, int32_t* seg_id);
 
 /* Template bank from chirp parameters (Sec. 3: one-second chirps over the
  * (f, fdot) plane).  Row k is
@@ -102,8 +110,8 @@ int bege_load_segment_device(bege_ctx* ctx, const float* strain_dev, int64_t n,
  * an exact fixed-point phase and FP64 sin/taper/norm, stored as FP32.
  * `params` is a HOST array of `count` chirps.  Errors: EINVAL, EBUDGET,
  * ENOMEM, ECUDA. */
-int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, double tau,
-                     double taper_frac, void* stream, int32_t* bank_id);
+BEGE_API int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, double tau,
+                              double taper_frac, void* stream, int32_t* bank_id);
 
 /* As bege_define_bank, with the time-symmetric chirps of the paper's banks
  * (Fig. 2 caption: each chirp superposed with itself backward in time, for
@@ -111,21 +119,22 @@ int bege_define_bank(bege_ctx* ctx, const bege_chirp* params, int64_t count, dou
  *     w_k[m] = T(m) (sin(2 pi phi(t_m)) + sin(2 pi phi(t_{L-1-m}))),
  * phi(t) = f0 t + fdot t^2 / 2, scaled to unit L2 norm (all zeros if the
  * two halves cancel).  Errors: as bege_define_bank. */
-int bege_define_bank_symmetric(bege_ctx* ctx, const bege_chirp* params, int64_t count,
-                               double tau, double taper_frac, void* stream, int32_t* bank_id);
+BEGE_API int bege_define_bank_symmetric(bege_ctx* ctx, const bege_chirp* params, int64_t count,
+                                        double tau, double taper_frac, void* stream,
+                                        int32_t* bank_id);
 
 /* Template bank from explicit samples: `samples` is a HOST array of
  * count x length FP32 values, row-major, used as given (no normalisation). */
-int bege_define_bank_samples(bege_ctx* ctx, const float* samples, int64_t count,
-                             int64_t length, void* stream, int32_t* bank_id);
+BEGE_API int bege_define_bank_samples(bege_ctx* ctx, const float* samples, int64_t count,
+                                      int64_t length, void* stream, int32_t* bank_id);
 
 /* Correlate segment `seg_id` with bank rows [k_begin, k_end) and keep the
  * tails |rho_k[n]| > kappa sigma_k (Eq. 3S, Eq. PT, Eq. tail).  Asynchronous:
  * enqueues the work on `stream` and returns a job handle at once.  The bank's
  * L must not exceed the segment's N.  kappa must be finite and >= 0.
  * Errors: EINVAL, EBUDGET, ENOMEM, ECUDA. */
-int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
-                   int64_t k_end, float kappa, void* stream, int32_t* job_id);
+BEGE_API int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                            int64_t k_end, float kappa, void* stream, int32_t* job_id);
 
 /* Wait for job `job_id` and copy its tail records to HOST `out` (capacity
  * records).  *n_total receives the true number of tails; *n_written the
@@ -133,8 +142,8 @@ int bege_correlate(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_beg
  * in device completion order (bege_sort_tails orders them).  Returns BEGE_EOVERFLOW (with the
  * counts filled in) when n_total exceeds what was copied, BEGE_ETIMEDOUT if
  * a bounded wait inside the kernel gave up (the job's results are invalid). */
-int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capacity,
-                     int64_t* n_written, int64_t* n_total);
+BEGE_API int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capacity,
+                              int64_t* n_written, int64_t* n_total);
 
 /* Several segments of one length against the same template range (Sec. 3.2:
  * a template's transform serves a block of segments, steps ii-iv): per
@@ -146,9 +155,9 @@ int bege_fetch_tails(bege_ctx* ctx, int32_t job_id, bege_tail* out, int64_t capa
  * N >= 2^14 and templates of at most 4096 samples.  Extra device memory
  * while the jobs live: 64 KB per resident CTA (about 20 MB).
  * Errors: EINVAL, EBUDGET, ENOMEM, ECUDA. */
-int bege_correlate_multi(bege_ctx* ctx, const int32_t* seg_ids, int32_t n_seg, int32_t bank_id,
-                         int64_t k_begin, int64_t k_end, float kappa, void* stream,
-                         int32_t* job_ids);
+BEGE_API int bege_correlate_multi(bege_ctx* ctx, const int32_t* seg_ids, int32_t n_seg,
+                                  int32_t bank_id, int64_t k_begin, int64_t k_end, float kappa,
+                                  void* stream, int32_t* job_ids);
 
 /* As bege_correlate, and the job also projects its hits onto one array of
  * the segment's N lags, keeping per lag the largest normalised value over
@@ -161,17 +170,17 @@ int bege_correlate_multi(bege_ctx* ctx, const int32_t* seg_ids, int32_t n_seg, i
  * post-callback race, Sec. 3.3, does not arise).  All-hit records are still
  * collected as for bege_correlate.  Extra device memory: 8 N bytes.
  * Errors: as bege_correlate. */
-int bege_correlate_max(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
-                       int64_t k_end, float kappa, void* stream, int32_t* job_id);
+BEGE_API int bege_correlate_max(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                                int64_t k_end, float kappa, void* stream, int32_t* job_id);
 
 /* As bege_correlate, with the tails restricted to a finite band (Sec. 5,
  * for deep searches with a low threshold): records (k, n, rho_k[n]) with
  * kappa_lo sigma_k < |rho_k[n]| < kappa_hi sigma_k.  Fetch them with
  * bege_fetch_tails.  Errors: as bege_correlate; EINVAL unless
  * 0 <= kappa_lo < kappa_hi, both finite. */
-int bege_correlate_band(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
-                        int64_t k_end, float kappa_lo, float kappa_hi, void* stream,
-                        int32_t* job_id);
+BEGE_API int bege_correlate_band(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                                 int64_t k_end, float kappa_lo, float kappa_hi, void* stream,
+                                 int32_t* job_id);
 
 /* Options of bege_correlate_ex; each field off (zero) gives bege_correlate. */
 typedef struct {
@@ -192,75 +201,75 @@ typedef struct {
  * the call only).  Records via bege_fetch_tails; a projection via
  * bege_fetch_max.  Errors: as bege_correlate; EINVAL for an invalid field
  * (linear and project must be 0 or 1). */
-int bege_correlate_ex(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
-                      int64_t k_end, const bege_search_opts* opts, void* stream,
-                      int32_t* job_id);
+BEGE_API int bege_correlate_ex(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                               int64_t k_end, const bege_search_opts* opts, void* stream,
+                               int32_t* job_id);
 
 /* Wait for a bege_correlate_max job and copy its projection to HOST arrays
  * of n = N entries: snr[n] = rho / sigma of the kept hit and tmpl[n] its
  * template index, or snr 0 and tmpl -1 where no template passes.
  * Errors: EINVAL (not such a job, n != N), ETIMEDOUT, ECUDA. */
-int bege_fetch_max(bege_ctx* ctx, int32_t job_id, float* snr, int32_t* tmpl, int64_t n);
+BEGE_API int bege_fetch_max(bege_ctx* ctx, int32_t job_id, float* snr, int32_t* tmpl, int64_t n);
 
 /* Sort n HOST tail records in place by (template, lag), the order in which
  * Sec. 3.3 gathers tails per template.  Host only (no context, no device);
  * (template, lag) pairs are unique within one job, so the order is total.
  * Errors: EINVAL (NULL records with n > 0, n < 0). */
-int bege_sort_tails(bege_tail* recs, int64_t n);
+BEGE_API int bege_sort_tails(bege_tail* recs, int64_t n);
 
 /* Wait for job `job_id` and report the device time in milliseconds of its
  * correlate kernel alone (CUDA events recorded on the job's stream right
  * before and after the launch).  Used for roofline accounting. */
-int bege_job_kernel_ms(bege_ctx* ctx, int32_t job_id, float* ms);
+BEGE_API int bege_job_kernel_ms(bege_ctx* ctx, int32_t job_id, float* ms);
 
 /* Non-blocking: BEGE_OK if the job has finished, BEGE_ENOTREADY if not. */
-int bege_query(bege_ctx* ctx, int32_t job_id);
+BEGE_API int bege_query(bege_ctx* ctx, int32_t job_id);
 
 /* Wait for job `job_id` and copy sigma_k (Eq. PT) for its rows to HOST `out`;
  * `count` must equal k_end - k_begin of the job. */
-int bege_get_sigma(bege_ctx* ctx, int32_t job_id, float* out, int64_t count);
+BEGE_API int bege_get_sigma(bege_ctx* ctx, int32_t job_id, float* out, int64_t count);
 
 /* Debug: the full correlation rho_k[0..N-1] for rows [k_begin, k_end) into
  * HOST `out` ((k_end - k_begin) x N floats, row-major).  Same kernel as
  * bege_correlate; synchronous on `stream`. */
-int bege_dump_correlation(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
-                          int64_t k_end, float* out, void* stream);
+BEGE_API int bege_dump_correlation(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                                   int64_t k_end, float* out, void* stream);
 
 /* Debug: the segment spectrum D_j, j = 0..N/2, as interleaved (re, im) FP32
  * into HOST `out` (N + 2 floats). */
-int bege_get_segment_spectrum(bege_ctx* ctx, int32_t seg_id, float* out);
+BEGE_API int bege_get_segment_spectrum(bege_ctx* ctx, int32_t seg_id, float* out);
 
 /* Debug: bank rows [k_begin, k_end) as FP32 into HOST `out` ((k_end-k_begin) x L). */
-int bege_get_bank_samples(bege_ctx* ctx, int32_t bank_id, int64_t k_begin, int64_t k_end,
-                          float* out);
+BEGE_API int bege_get_bank_samples(bege_ctx* ctx, int32_t bank_id, int64_t k_begin, int64_t k_end,
+                                   float* out);
 
 /* Segment length N / bank template length L of a handle (0 if unknown). */
-int64_t bege_segment_length(bege_ctx* ctx, int32_t seg_id);
-int64_t bege_bank_length(bege_ctx* ctx, int32_t bank_id);
+BEGE_API int64_t bege_segment_length(bege_ctx* ctx, int32_t seg_id);
+BEGE_API int64_t bege_bank_length(bege_ctx* ctx, int32_t bank_id);
 
 /* Device bytes currently owned by the context. */
-uint64_t bege_device_bytes(const bege_ctx* ctx);
+BEGE_API uint64_t bege_device_bytes(const bege_ctx* ctx);
 
 /* Launch shapes of the correlate kernel for segment length n.  A shape is
  * (columns per CTA, threads per CTA); the cluster holds (n / 8192) / columns
  * CTAs.  bege_list_configs writes up to `max` pairs into `out` as
  * {nc0, threads0, nc1, threads1, ...} and the number available into *count. */
-int bege_list_configs(bege_ctx* ctx, int64_t n, int32_t* out, int32_t max, int32_t* count);
+BEGE_API int bege_list_configs(bege_ctx* ctx, int64_t n, int32_t* out, int32_t max, int32_t* count);
 
 /* Select the launch shape used by later bege_correlate calls for length n.
  * EINVAL if the shape is not one of bege_list_configs. */
-int bege_set_config(bege_ctx* ctx, int64_t n, int32_t nc, int32_t threads);
+BEGE_API int bege_set_config(bege_ctx* ctx, int64_t n, int32_t nc, int32_t threads);
 
 /* The launch shape currently used for length n (the default if none set). */
-int bege_get_config(bege_ctx* ctx, int64_t n, int32_t* nc, int32_t* threads);
+BEGE_API int bege_get_config(bege_ctx* ctx, int64_t n, int32_t* nc, int32_t* threads);
 
 /* Autotuner (batching form): time every launch shape for the segment's n on
  * bank rows [k_begin, k_end) of `bank_id` (`reps` timed runs each after one
  * warm-up, median of the kernel time), select the fastest for that n and
  * report its median time in *best_ms.  Synchronous on `stream`; the results
  * of the timing runs are discarded. */
-int bege_autotune(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin, int64_t k_end,
-                  int32_t reps, void* stream, float* best_ms);
+BEGE_API int bege_autotune(bege_ctx* ctx, int32_t seg_id, int32_t bank_id, int64_t k_begin,
+                           int64_t k_end, int32_t reps, void* stream, float* best_ms);
 
 /* ---- Batching form ------------------------------------------------------
  * Many segments of different lengths, each against its own bank range, in
@@ -284,41 +293,41 @@ typedef struct {
  * sigma and tail buffers (`tail_capacity` records per entry, 0 = the
  * context default) and captures the graph.  *batch_id receives the handle
  * (released with bege_release).  Errors: EINVAL, EBUDGET, ENOMEM, ECUDA. */
-int bege_batch_create(bege_ctx* ctx, const bege_batch_entry* entries, int32_t count,
-                      uint64_t tail_capacity, void* stream, int32_t* batch_id);
+BEGE_API int bege_batch_create(bege_ctx* ctx, const bege_batch_entry* entries, int32_t count,
+                               uint64_t tail_capacity, void* stream, int32_t* batch_id);
 
 /* Launch the batch's graph on `stream` (asynchronous): segment spectra of
  * every entry, then all correlations.  Each run overwrites the previous
  * run's results. */
-int bege_batch_run(bege_ctx* ctx, int32_t batch_id, void* stream);
+BEGE_API int bege_batch_run(bege_ctx* ctx, int32_t batch_id, void* stream);
 
 /* Wait for the last run and report its device time (CUDA events around the
  * graph launch) in milliseconds. */
-int bege_batch_elapsed_ms(bege_ctx* ctx, int32_t batch_id, float* ms);
+BEGE_API int bege_batch_elapsed_ms(bege_ctx* ctx, int32_t batch_id, float* ms);
 
 /* Wait for the last run and copy entry `entry`'s tails / sigma to HOST
  * memory; same conventions as bege_fetch_tails / bege_get_sigma. */
-int bege_batch_fetch_tails(bege_ctx* ctx, int32_t batch_id, int32_t entry, bege_tail* out,
-                           int64_t capacity, int64_t* n_written, int64_t* n_total);
-int bege_batch_get_sigma(bege_ctx* ctx, int32_t batch_id, int32_t entry, float* out,
-                         int64_t count);
+BEGE_API int bege_batch_fetch_tails(bege_ctx* ctx, int32_t batch_id, int32_t entry, bege_tail* out,
+                                    int64_t capacity, int64_t* n_written, int64_t* n_total);
+BEGE_API int bege_batch_get_sigma(bege_ctx* ctx, int32_t batch_id, int32_t entry, float* out,
+                                  int64_t count);
 
 /* Execution plan of a batch.  plan 0: the persistent kernel (clusters of 8
  * CTAs taking work items of `chunk` templates from a queue; `order` 0 =
  * longest segments first, 1 = entries interleaved); plan 1: one launch per
  * entry with the per-length launch shape of bege_set_config. */
-int bege_batch_set_plan(bege_ctx* ctx, int32_t batch_id, int32_t plan, int64_t chunk,
-                        int32_t order);
-int bege_batch_get_plan(bege_ctx* ctx, int32_t batch_id, int32_t* plan, int64_t* chunk,
-                        int32_t* order);
+BEGE_API int bege_batch_set_plan(bege_ctx* ctx, int32_t batch_id, int32_t plan, int64_t chunk,
+                                 int32_t order);
+BEGE_API int bege_batch_get_plan(bege_ctx* ctx, int32_t batch_id, int32_t* plan, int64_t* chunk,
+                                 int32_t* order);
 
 /* Autotuner of the batching form: times every plan (plan 0 over chunks of
  * 64..2048 templates and both orders, plan 1 with the current per-length
  * shapes) with `reps` runs each after one warm-up, keeps the fastest (the
  * per-segment plan only if more than 1% faster than the best persistent one)
  * and reports its median time in *best_ms.  Synchronous on `stream`. */
-int bege_batch_autotune(bege_ctx* ctx, int32_t batch_id, int32_t reps, void* stream,
-                        float* best_ms);
+BEGE_API int bege_batch_autotune(bege_ctx* ctx, int32_t batch_id, int32_t reps, void* stream,
+                                 float* best_ms);
 
 /* ---- Serving form ----------------------------------------------------------
  * A request loop with continuous batching over one resident bank (the paper's
@@ -357,35 +366,37 @@ typedef struct {
 } bege_serve_info;
 
 /* Start a server thread on `cfg->bank_id`.  *server_id receives the handle. */
-int bege_serve_create(bege_ctx* ctx, const bege_serve_config* cfg, int32_t* server_id);
+BEGE_API int bege_serve_create(bege_ctx* ctx, const bege_serve_config* cfg, int32_t* server_id);
 
 /* Queue a request: `strain` is a HOST array of n FP32 samples (copied before
  * the call returns; n a power of two in [2^10, 2^17], at least the bank's
  * template length).  *request_id receives a per-server id. */
-int bege_serve_submit(bege_ctx* ctx, int32_t server_id, const float* strain, int64_t n,
-                      int32_t channel, int64_t* request_id);
+BEGE_API int bege_serve_submit(bege_ctx* ctx, int32_t server_id, const float* strain, int64_t n,
+                               int32_t channel, int64_t* request_id);
 
 /* Block until the request is done (BEGE_OK), failed (its error), or
  * `timeout_ms` passes (BEGE_ETIMEDOUT; < 0 waits without limit). */
-int bege_serve_wait(bege_ctx* ctx, int32_t server_id, int64_t request_id, int32_t timeout_ms);
+BEGE_API int bege_serve_wait(bege_ctx* ctx, int32_t server_id, int64_t request_id,
+                             int32_t timeout_ms);
 
 /* State and timings of a request. */
-int bege_serve_info_get(bege_ctx* ctx, int32_t server_id, int64_t request_id,
-                        bege_serve_info* info);
+BEGE_API int bege_serve_info_get(bege_ctx* ctx, int32_t server_id, int64_t request_id,
+                                 bege_serve_info* info);
 
 /* Results of a done request, from host memory: tails (same conventions as
  * bege_fetch_tails) and sigma of every bank row (`count` = bank size). */
-int bege_serve_fetch_tails(bege_ctx* ctx, int32_t server_id, int64_t request_id, bege_tail* out,
-                           int64_t capacity, int64_t* n_written, int64_t* n_total);
-int bege_serve_get_sigma(bege_ctx* ctx, int32_t server_id, int64_t request_id, float* out,
-                         int64_t count);
+BEGE_API int bege_serve_fetch_tails(bege_ctx* ctx, int32_t server_id, int64_t request_id,
+                                    bege_tail* out, int64_t capacity, int64_t* n_written,
+                                    int64_t* n_total);
+BEGE_API int bege_serve_get_sigma(bege_ctx* ctx, int32_t server_id, int64_t request_id, float* out,
+                                  int64_t count);
 
 /* Drop a done request's host-side results. */
-int bege_serve_forget(bege_ctx* ctx, int32_t server_id, int64_t request_id);
+BEGE_API int bege_serve_forget(bege_ctx* ctx, int32_t server_id, int64_t request_id);
 
 /* Stop the server after the work in flight completes; queued requests that
  * were not admitted are dropped. */
-int bege_serve_destroy(bege_ctx* ctx, int32_t server_id);
+BEGE_API int bege_serve_destroy(bege_ctx* ctx, int32_t server_id);
 
 /* ---- Search without device allocation -----------------------------------
  * The paper has no counterpart of this call.  It serves callers that may not
@@ -420,22 +431,23 @@ int bege_serve_destroy(bege_ctx* ctx, int32_t server_id);
  * call's contents and is shared by all calls on a device: calls whose work
  * overlaps on the GPU race and must be serialised by the caller.  Errors:
  * EINVAL (sizes, alignment, NULL), ECUDA. */
-int bege_search_noalloc(const float* strain_dev, int64_t n, const float* bank_dev, int64_t ld,
-                        int64_t k_begin, int64_t k_end, float kappa, float* sigma_dev,
-                        bege_tail* tails_dev, uint64_t tail_capacity,
-                        unsigned long long* tail_count_dev, void* stream);
+BEGE_API int bege_search_noalloc(const float* strain_dev, int64_t n, const float* bank_dev,
+                                 int64_t ld, int64_t k_begin, int64_t k_end, float kappa,
+                                 float* sigma_dev, bege_tail* tails_dev,
+                                 uint64_t tail_capacity, unsigned long long* tail_count_dev,
+                                 void* stream);
 
 /* Release a segment, bank, job or batch handle and its device memory (job
  * buffers return to the context's pool).  Errors: EINVAL for an unknown
  * handle. */
-int bege_release(bege_ctx* ctx, int32_t handle);
+BEGE_API int bege_release(bege_ctx* ctx, int32_t handle);
 
 /* Message of the last error on the calling thread ("" if none).  ctx may be
  * NULL. */
-const char* bege_last_error(const bege_ctx* ctx);
+BEGE_API const char* bege_last_error(const bege_ctx* ctx);
 
 /* Library version string. */
-const char* bege_version(void);
+BEGE_API const char* bege_version(void);
 
 #ifdef __cplusplus
 }

@@ -18,6 +18,7 @@ LIB = os.path.join(HERE, "libbege.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+          "-Xcompiler", "-fvisibility=hidden",
           "-I", os.path.join(HERE, "..", "include")]
 SOURCES = ["bege_corr_tc.cu", "bege_corr_multi.cu", "bege_corr_s16.cu", "bege_corr_s8.cu", "bege_corr_s4.cu", "bege_corr_s2.cu",
            "bege_corr_s1.cu", "bege_segment_bank.cu", "bege_batch.cu", "bege_noalloc.cu", "bege_api.cpp",
