@@ -89,20 +89,24 @@ def run_sharded(dist, compute, count: int, chunk: int, fail_rank: int | None = N
     """Search rows [0, count) over all ranks of ``dist`` (an initialised
     torch.distributed module) in chunks of ``chunk`` rows.
 
-    ``compute(k0, k1)`` returns this rank's tail records for rows [k0, k1).
-    Chunks are dealt round-robin; after every round the ranks exchange (on
-    the host, via all_gather_object) which chunks they finished.  A rank
-    that raises is treated as failed: it reports no more progress, and its
-    unfinished chunks are dealt again to the survivors.  ``fail_rank`` /
-    ``fail_after`` make that rank fail after that many chunks (fault
-    injection for tests).  Returns the merged tails on rank 0 (None
-    elsewhere) and the set of ranks that failed.
+    ``compute(k0, k1)`` returns this rank's tail records for rows [k0, k1),
+    or a pair (records, (snr, tmpl)) with the chunk's per-lag maximum
+    (Eq. Ak over those rows, as bege_fetch_max returns it).  Chunks are
+    dealt round-robin; after every round the ranks exchange (on the host,
+    via all_gather_object) which chunks they finished.  A rank that raises
+    is treated as failed: it reports no more progress, and its unfinished
+    chunks are dealt again to the survivors.  ``fail_rank`` / ``fail_after``
+    make that rank fail after that many chunks (fault injection for tests).
+    Returns the merged tails on rank 0 (None elsewhere) and the set of ranks
+    that failed; with projections, also the merged per-lag maximum over the
+    whole bank (every rank), from one all_reduce(MAX) of the packed keys.
     """
     rank, world = dist.get_rank(), dist.get_world_size()
     pending = [(k, min(k + chunk, count)) for k in range(0, count, chunk)]
     alive = list(range(world))
     failed: set[int] = set()
     mine: list[np.ndarray] = []
+    proj_key = None  # this rank's per-lag maximum over its finished chunks
     done_here = 0
     dead = False
     while pending:
@@ -116,7 +120,12 @@ def run_sharded(dist, compute, count: int, chunk: int, fail_rank: int | None = N
                 try:
                     if fail_rank == rank and done_here >= fail_after:
                         raise RuntimeError(f"rank {rank} failed (injected)")
-                    mine.append(compute(*c))
+                    res = compute(*c)
+                    if isinstance(res, tuple):
+                        res, (snr, tmpl) = res
+                        key = projection_key(snr, tmpl)
+                        proj_key = key if proj_key is None else np.maximum(proj_key, key)
+                    mine.append(res)
                     finished.append(c)
                     done_here += 1
                 except RuntimeError:
@@ -134,6 +143,15 @@ def run_sharded(dist, compute, count: int, chunk: int, fail_rank: int | None = N
             raise RuntimeError("every rank failed")
     gathered = [None] * world
     dist.all_gather_object(gathered, merge_tails(mine))
-    if rank == 0:
-        return merge_tails(gathered), failed
-    return None, failed
+    tails = merge_tails(gathered) if rank == 0 else None
+    # projections: every rank learns the length, ranks without a finished
+    # chunk contribute zeros (no hit), then one MAX reduction of the keys
+    lengths = [None] * world
+    dist.all_gather_object(lengths, None if proj_key is None else len(proj_key))
+    n = max((x for x in lengths if x is not None), default=None)
+    if n is None:
+        return tails, failed
+    import torch
+    key = torch.from_numpy(proj_key if proj_key is not None else np.zeros(n, np.int64))
+    dist.all_reduce(key, op=dist.ReduceOp.MAX)
+    return tails, failed, projection_from_key(key.numpy())

@@ -127,3 +127,47 @@ def test_merge_projections_keeps_max_and_smaller_template_on_ties():
     assert np.array_equal(s1, a_snr) and np.array_equal(t1, a_tm)
     with pytest.raises(ValueError):
         shard.merge_projections([(np.array([-1.0], np.float32), np.array([0], np.int32))])
+
+
+def sharded_max_worker(rank, world, port, fail_rank, out_dir):
+    """run_sharded with per-chunk projections: chunks of the bank searched
+    by the oracle (tails and the per-lag maximum of the chunk's rows), a
+    rank failing after one chunk, the projection merged over every chunk."""
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    y, bank, O = small_problem()
+
+    def compute(k0, k1):
+        res = O.search(y, bank[k0:k1], 2.5, k0=k0, return_rho=True)
+        t = res["tails"]
+        out = np.empty(len(t), dtype=[("tmpl", np.uint32), ("lag", np.uint32),
+                                      ("value", np.float32)])
+        out["tmpl"], out["lag"], out["value"] = t["tmpl"], t["lag"], t["value"]
+        return out, O.max_projection(res["rho"], res["sigma"], 2.5, k0=k0)
+
+    tails, failed, (snr, tmpl) = shard.run_sharded(dist, compute, len(bank), 3,
+                                                   fail_rank=fail_rank, fail_after=1)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "proj2.npy"), np.stack([snr, tmpl.astype(np.float32)]))
+        np.save(os.path.join(out_dir, "meta2.npy"), np.array([len(tails), len(failed)]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("fail_rank", [None, 1])
+def test_sharded_search_merges_projections(tmp_path, fail_rank):
+    world = 2
+    mp.start_processes(sharded_max_worker, args=(world, free_port(), fail_rank, str(tmp_path)),
+                       nprocs=world, start_method="spawn")
+    m_snr, m_tmpl = np.load(tmp_path / "proj2.npy")
+    n_tails, n_failed = np.load(tmp_path / "meta2.npy")
+    y, bank, O = small_problem()
+    res = O.search(y, bank, 2.5, return_rho=True)
+    snr, tmpl = O.max_projection(res["rho"], res["sigma"], 2.5)
+    assert np.sum(tmpl >= 0) > 20
+    assert np.array_equal(m_tmpl.astype(np.int32), tmpl)
+    assert np.array_equal(m_snr, snr.astype(np.float32))
+    assert n_tails == len(res["tails"])
+    assert n_failed == (0 if fail_rank is None else 1)
