@@ -232,7 +232,8 @@ def correlate_source_hash() -> str:
     src = os.path.join(ROOT, "paper_1708_01609_gb300", "csrc")
     h = hashlib.sha256()
     for name in CORRELATE_SOURCES:
-        h.update(open(os.path.join(src, name), "rb").read())
+        with open(os.path.join(src, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()
 
 
@@ -242,7 +243,8 @@ def _counter_record():
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path)).get("correlate_kernel")
+    with open(path) as f:
+        rec = json.load(f).get("correlate_kernel")
     if not rec or rec.get("source_sha256") != correlate_source_hash():
         return None
     return rec

@@ -15,7 +15,8 @@ HEADER = os.path.join(ROOT, "include", "bege.h")
 
 
 def declared_symbols():
-    text = open(HEADER).read()
+    with open(HEADER) as f:
+        text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(bege_[a-z_]+)\s*\(", text)))
 

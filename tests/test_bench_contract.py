@@ -42,7 +42,8 @@ def test_reference_arm_other_ranks_exit_quietly():
 def test_counter_record_is_tied_to_the_source(tmp_path, monkeypatch):
     sys.path.insert(0, ROOT)
     import bench
-    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["correlate_kernel"]
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)["correlate_kernel"]
     assert rec["dram_bytes_per_correlation"] > 16384  # at least the template itself
     assert set(rec["counters"]) >= {"sm__pipe_fma_cycles_active_pct", "smsp__issue_active_pct"}
     monkeypatch.setattr(bench, "correlate_source_hash", lambda: "0" * 64)

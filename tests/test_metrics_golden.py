@@ -11,7 +11,9 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_figures.txt")
 
 def golden():
     out = {}
-    for line in open(GOLDEN):
+    with open(GOLDEN) as fh:
+        lines = fh.readlines()
+    for line in lines:
         if line.startswith("#") or not line.strip():
             continue
         name, value, rel, _ = [f.strip() for f in line.split("|", 3)]
