@@ -417,17 +417,18 @@ BEGE_API int bege_serve_destroy(bege_ctx* ctx, int32_t server_id);
  *                   holds template k, zero beyond its length
  *   ld              row stride in floats, a multiple of 8, at most n
  *   kappa           finite, >= 0
- *   sigma_dev       DEVICE, k_end - k_begin FP32: sigma of row k at k - k_begin
- *   tails_dev       DEVICE, tail_capacity records (bege_tail)
+ *   sigma_dev       DEVICE, k_end - k_begin FP32: sigma of row k at k - k_begin,
+ *                   4-byte aligned
+ *   tails_dev       DEVICE, tail_capacity records (bege_tail), 4-byte aligned
  *   tail_count_dev  DEVICE, one unsigned 64-bit count, 8-byte aligned; set to
  *                   zero by the call, then to the true number of tails (only
  *                   the first tail_capacity records are stored)
  *   stream          cudaStream_t as void*; the call only enqueues work
  *
  * The first call on a device looks up the scratch array's device address
- * (with that device current) and every call with a new n recomputes the
- * twiddle tables in the scratch array, so the first call on each device
- * should come before any stream capture.  The scratch array keeps the last
+ * (with that device current), so the first call on each device should come
+ * before any stream capture.  Every call recomputes the twiddle tables for
+ * its n in the scratch array on `stream`, ahead of its other kernels.  The scratch array keeps the last
  * call's contents and is shared by all calls on a device: calls whose work
  * overlaps on the GPU race and must be serialised by the caller.  Errors:
  * EINVAL (sizes, alignment, NULL), ECUDA. */

@@ -10,7 +10,9 @@
 // file-scope device array of fixed size instead:
 //   - the product coefficients A, B and the segment spectrum D of the
 //     segment (at most N = 2^16 samples),
-//   - the FP32 twiddle tables for that N (computed on the device in FP64).
+//   - the FP32 twiddle tables for that N (computed on the device in FP64
+//     by every call, ahead of the call's own kernels on its stream, so no
+//     call depends on what an earlier call left in the array).
 // The array lives on every GPU that loads the library until the process
 // exits (about 1.05 MiB).  All calls on a device share it and it keeps the
 // contents of the last call, so two calls whose work overlaps on the GPU
@@ -97,12 +99,11 @@ __global__ void search_tables_kernel(Geometry g, float2* tw2, float2* tw3, float
   }
 }
 
-// Per-device set-up: the device address of the scratch array (looked up once
-// per device, with that device current) and the N whose tables it holds.
+// Per-device set-up: the device address of the scratch array, looked up once
+// per device with that device current.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {};
-int64_t g_tables_n[kMaxDevices] = {};
 
 }  // namespace
 
@@ -128,7 +129,8 @@ extern "C" int bege_search_noalloc(const float* strain_dev, int64_t n, const flo
   if (!(kappa >= 0.f) || kappa > 3.0e38f)
     return set_last_error(BEGE_EINVAL, "bege_search_noalloc: kappa must be finite and >= 0");
   if (reinterpret_cast<uintptr_t>(strain_dev) % 8 || reinterpret_cast<uintptr_t>(bank_dev) % 32 ||
-      reinterpret_cast<uintptr_t>(tail_count_dev) % 8)
+      reinterpret_cast<uintptr_t>(tail_count_dev) % 8 ||
+      reinterpret_cast<uintptr_t>(sigma_dev) % 4 || reinterpret_cast<uintptr_t>(tails_dev) % 4)
     return set_last_error(BEGE_EINVAL, "bege_search_noalloc: misaligned buffer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0;
@@ -159,15 +161,15 @@ extern "C" int bege_search_noalloc(const float* strain_dev, int64_t n, const flo
     p.w16S = reinterpret_cast<const float2*>(base + kOffW16S);
     p.wS = reinterpret_cast<const float2*>(base + kOffWS);
     p.wN = reinterpret_cast<const float2*>(base + kOffWN);
-    if (g_tables_n[dev] != n) {
-      search_tables_kernel<<<64, 256, 0, s>>>(
-          g, const_cast<float2*>(p.tw2), const_cast<float2*>(p.tw3), const_cast<float2*>(p.wH),
-          const_cast<float2*>(p.wR0S), const_cast<float2*>(p.w16S), const_cast<float2*>(p.wS),
-          const_cast<float2*>(p.wN));
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return set_last_error(BEGE_ECUDA, cudaGetErrorString(e));
-      g_tables_n[dev] = n;
-    }
+    // The tables are rebuilt on every call, in stream order before this
+    // call's kernels: the host keeps no record of which n the array holds,
+    // which could disagree with the device's order of work.
+    search_tables_kernel<<<64, 256, 0, s>>>(
+        g, const_cast<float2*>(p.tw2), const_cast<float2*>(p.tw3), const_cast<float2*>(p.wH),
+        const_cast<float2*>(p.wR0S), const_cast<float2*>(p.w16S), const_cast<float2*>(p.wS),
+        const_cast<float2*>(p.wN));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_last_error(BEGE_ECUDA, cudaGetErrorString(e));
     float4* AB = reinterpret_cast<float4*>(base + kOffAB);
     float2* D = reinterpret_cast<float2*>(base + kOffD);
     e = launch_segment(p, strain_dev, D, AB, s);

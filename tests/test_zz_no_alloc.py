@@ -4,11 +4,13 @@ example a framework's pool or an arena reserved at start-up).
 
 The caller allocates every input and output here (with torch, standing in
 for the caller's own allocator) and the library uses only its fixed scratch
-array.  Two calls in a row, with different segment lengths so the second call
-also rebuilds the twiddle tables in the scratch array, must agree with the
-regular entry points (load segment, define bank, correlate, fetch) within the
-tolerances of the other GPU tests: sigma within 1e-6 relative, tail values
-within 1e-5 sigma, tail sets identical away from the threshold.
+array.  Three calls in a row, with different segment lengths (2^16 and 2^14
+split into columns; 2^11 a single column, whose twiddle tables only this
+call's table kernel writes), must agree with the regular entry points (load
+segment, define bank, correlate, fetch) within the tolerances of the other
+GPU tests: sigma within 1e-6 relative, tail values within 1e-5 sigma, tail
+sets identical away from the threshold.  The first call is also checked
+against the FP64 oracle with the same rule.
 
 This file is named to be collected last so that a run stopping at the first
 failure has already run every other test.
@@ -16,8 +18,9 @@ failure has already run every other test.
 import numpy as np
 import pytest
 
+import oracle as O
 import synthetic as S
-from gpu_helpers import NEAR, TOL_FP32, make_ctx
+from gpu_helpers import NEAR, TOL_FP32, compare_tails, make_ctx
 
 pytestmark = pytest.mark.gpu
 
@@ -64,10 +67,18 @@ def case(n, count, length, seed):
 def test_noalloc_matches_regular_entry_points_two_calls():
     from paper_1708_01609_gb300.binding import BegeError, bege_search_noalloc
     ctx = make_ctx(tail_capacity=1 << 20)
-    calls = [(1 << 16, 24, 4096, 0, 24, 4.5, 11), (1 << 14, 40, 2048, 3, 40, 4.5, 12)]
-    for n, count, length, k0, k1, kappa, seed in calls:
+    calls = [(1 << 16, 24, 4096, 0, 24, 4.5, 11), (1 << 14, 40, 2048, 3, 40, 4.5, 12),
+             (1 << 11, 16, 512, 2, 16, 4.0, 13)]
+    for i, (n, count, length, k0, k1, kappa, seed) in enumerate(calls):
         y, bank = case(n, count, length, seed)
         got, got_total, got_sig = noalloc_search(y, bank, k0, k1, kappa, cap=1 << 16)
+        if i == 0:
+            # the same call against the FP64 oracle
+            ref_o = O.search(y, bank[k0:k1].astype(np.float64), np.inf, k0=k0, batch=8,
+                             return_rho=True)
+            assert np.all(np.abs(got_sig / ref_o["sigma"] - 1) <= 1e-6)
+            compare_tails(got, {k0 + r: (ref_o["rho"][r], ref_o["sigma"][r])
+                                for r in range(k1 - k0)}, kappa)
         ref, ref_total, ref_sig = regular_search(ctx, y, bank, k0, k1, kappa)
         assert got_total == len(got) and ref_total == len(ref) and got_total > 0
         assert np.all(np.abs(got_sig / ref_sig - 1) <= 1e-6)
@@ -86,4 +97,10 @@ def test_noalloc_matches_regular_entry_points_two_calls():
         bege_search_noalloc(1 << 20, 1 << 17, 1 << 20, 4096, 0, 1, 5.0, 1 << 20, 1 << 20, 1,
                             1 << 20)
     assert err.value.code == -1 and "2^16" in str(err.value)
+    # so are output buffers that the kernels' 4-byte stores could not use
+    for sig_p, tails_p in ((1 << 20, (1 << 20) + 2), ((1 << 20) + 1, 1 << 20)):
+        with pytest.raises(BegeError) as err:
+            bege_search_noalloc(1 << 20, 1 << 14, 1 << 20, 4096, 0, 1, 5.0, sig_p, tails_p, 1,
+                                1 << 20)
+        assert err.value.code == -1 and "misaligned" in str(err.value)
     ctx.close()
