@@ -13,8 +13,9 @@ The metric is chirp correlations per second (templates x segments / s).
 
 With N > 1 it runs under torch.distributed.run, one rank per GPU, each rank
 searching its own segment against the full bank (weak scaling; no collective
-on the data path, only the barrier and the max-over-ranks time).  Rank 0
-prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+on the data path, only the barrier and the max-over-ranks time), or with
+``--shard`` one segment against the bank split into one contiguous row range
+per rank (strong scaling).  Rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
 """
 from __future__ import annotations
@@ -45,7 +46,7 @@ UNIT = "correlations/s"
 PRECISIONS = {"fp32": 0, "bf16x3": 1, "fp16x3": 2}
 
 
-def workload_config(templates: int, world: int) -> dict:
+def workload_config(templates: int, world: int, shard: bool = False) -> dict:
     return {
         "workload": (f"N=2^16 band-limited (350-2000 Hz) strain segment x {templates} chirp "
                      "templates (1024 f0 x 1024 fdot grid, tau 1 s, 5% taper), kappa 5.5, "
@@ -55,7 +56,10 @@ def workload_config(templates: int, world: int) -> dict:
         "kappa": KAPPA,
         "fs_hz": 4096.0,
         "l2": "inputs larger than L2: the 17.2 GB FP32 bank is streamed from HBM every step",
-        "parallelism": f"{world} independent replica(s), one segment per GPU per step",
+        "parallelism": (f"bank split into {world} contiguous row range(s), one per GPU, the "
+                        "same segment on every GPU; tails stay on each rank's host"
+                        if shard else
+                        f"{world} independent replica(s), one segment per GPU per step"),
     }
 
 
@@ -287,11 +291,15 @@ def run_ours(args):
     prec = PRECISIONS[args.precision]
     ctx = binding.Context(local, tail_capacity=cap, precision=prec)
     templates = args.templates
-    seg_data, params = S.paper_case(seed=2017 + rank)
+    seg_data, params = S.paper_case(seed=2017 + (0 if args.shard else rank))
     params = params[:templates]
+    # --shard: this rank holds and searches only its own rows of the bank
+    from paper_1708_01609_gb300 import shard
+    k0, k1 = shard.shard_ranges(templates, world)[rank] if args.shard else (0, templates)
+    rows = k1 - k0
     stream_obj = torch.cuda.current_stream()
     stream = stream_obj.cuda_stream
-    bank = ctx.bege_define_bank(params, tau=1.0, taper_frac=0.05, stream=stream)
+    bank = ctx.bege_define_bank(params[k0:k1], tau=1.0, taper_frac=0.05, stream=stream)
     y_dev = torch.from_numpy(seg_data.y).cuda()
     y_pin = torch.from_numpy(seg_data.y).pin_memory()
     y_host = y_pin.numpy()
@@ -303,7 +311,7 @@ def run_ours(args):
             seg = ctx.bege_load_segment(y_host, 0, stream)
         else:
             seg = ctx.bege_load_segment_device(y_dev.data_ptr(), N_SAMPLES, 0, stream)
-        job = ctx.bege_correlate(seg, bank, 0, templates, KAPPA, stream)
+        job = ctx.bege_correlate(seg, bank, 0, rows, KAPPA, stream)
         recs, total = ctx.bege_fetch_tails(job, out=out)
         if len(recs) != total:
             raise RuntimeError(f"tail buffer overflow: {total} tails, {len(recs)} copied")
@@ -347,7 +355,7 @@ def run_ours(args):
         step(True)
     ms_e2e, tails_e2e, _, _ = timed(True, args.steps)
 
-    units = templates * world * args.steps
+    units = templates * (1 if args.shard else world) * args.steps
     value = units / (ms / 1e3)
     value_e2e = units / (ms_e2e / 1e3)
     props = torch.cuda.get_device_properties(local)
@@ -355,15 +363,15 @@ def run_ours(args):
     sm_max = peaks.get("sm_max_mhz") or 2070.0
     peak = metrics.fp32_peak_flops(props.multi_processor_count, sm_max)
     kernel_ms = statistics.mean(kms)
-    flops_launch = templates * metrics.nominal_flops_per_correlation(N_SAMPLES)
+    flops_launch = rows * metrics.nominal_flops_per_correlation(N_SAMPLES)
     achieved = flops_launch / (kernel_ms / 1e3)
-    traffic = traffic_record(templates)
+    traffic = traffic_record(rows)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(templates, world),
+        "scaling": "strong" if args.shard else "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(templates, world, args.shard),
         "roofline": {
             "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
@@ -391,6 +399,16 @@ def run_ours(args):
         line["precision_form"] = {
             name: precision_form(PRECISIONS[name], seg_data, params, templates, args, value, local)
             for name in ("bf16x3", "fp16x3")}
+    if rank == 0 and world == 1 and args.precision == "fp32" and not args.no_serving:
+        if ctx is not None:
+            ctx.close()
+            ctx = None
+        line["serving"] = serving_form(args, local)
+    if rank == 0 and world == 1 and args.precision == "fp32" and not args.no_batch:
+        if ctx is not None:
+            ctx.close()
+            ctx = None
+        line["batch"] = batch_form(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -544,27 +562,38 @@ def precision_form(prec: int, seg_data, params, templates: int, args, fp32_value
     value = templates * args.steps / (ms / 1e3)
     kernel_ms = statistics.mean(r[1] for r in res)
     peaks = measured_peaks()
-    tflops = templates * tc_flops_per_template(N_SAMPLES) / (kernel_ms / 1e3) / 1e12
-    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    fp32_peak = metrics.fp32_peak_flops(torch.cuda.get_device_properties(device).multi_processor_count,
+                                        peaks.get("sm_max_mhz") or 2070.0) / 1e12
+    method = templates * metrics.nominal_flops_per_correlation(N_SAMPLES) / (kernel_ms / 1e3) / 1e12
+    mma = templates * tc_flops_per_template(N_SAMPLES) / (kernel_ms / 1e3) / 1e12
     return {"value": value, "unit": UNIT, "ms_per_step": ms / args.steps, "kernel_ms": kernel_ms,
             "vs_fp32_path": value / fp32_value, "tails_per_step": statistics.mean(r[0] for r in res),
-            "tensor": {"achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                       "basis": "dense MMA flops incl. split terms; peak = sustained bf16 of "
-                                "MEASURED_PEAKS.json (FP16 has the same dense rate)"},
+            "method_work": {"achieved": method, "unit": "TFLOP/s",
+                            "frac_of_fp32_peak": method / fp32_peak,
+                            "frac_of_bf16_peak": method / bf16_peak,
+                            "fp32_peak": fp32_peak, "bf16_peak": bf16_peak,
+                            "basis": "the method's nominal 5 N log2 N flops per correlation "
+                                     "(Eq. nd) over the kernel's CUDA-event time; peaks: FP32 "
+                                     "ALU (SMs x 128 x 2 x max SM clock) and the measured "
+                                     "sustained bf16 of MEASURED_PEAKS.json"},
+            "mma_pipe": {"achieved": mma, "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": mma / bf16_peak,
+                         "basis": "diagnostic: dense MMA flops issued, including the three "
+                                  "split terms, against the measured sustained bf16 peak (FP16 "
+                                  "has the same dense rate)"},
             "error_bar_sigma": 2e-3}
 
 
-def run_batch_form(args):
+def batch_form(args, device: int = 0) -> dict:
     """Batching form: 64 segments, N uniform over 2^14..2^17, each against
     its own sub-bank of 2^12..2^16 chirps (tau 0.5 s or 1 s), 8 injections
     each; one persistent launch in a CUDA graph per step, plan chosen by the
-    batch autotuner."""
+    batch autotuner.  Graph launches timed with CUDA events on the launching
+    stream, with the clocks sampled meanwhile."""
     import torch
-    from paper_1708_01609_gb300 import binding, build
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA GPU")
-    build()
-    ctx = binding.Context(0, tail_capacity=1 << 22)
+    from paper_1708_01609_gb300 import binding
+    ctx = binding.Context(device, tail_capacity=1 << 22)
     entries, grids = S.batch_case()
     stream_obj = torch.cuda.current_stream()
     stream = stream_obj.cuda_stream
@@ -574,55 +603,75 @@ def run_batch_form(args):
     batch = ctx.bege_batch_create(spec, stream=stream)
     tuned_ms = ctx.bege_batch_autotune(batch, reps=2, stream=stream)
     plan = ctx.bege_batch_get_plan(batch)
-    for _ in range(args.warmup):
+    steps = max(3, min(args.steps, 10))
+    for _ in range(max(3, args.warmup)):
         ctx.bege_batch_run(batch, stream)
     torch.cuda.synchronize()
+    clocks = ClockSampler(device)
+    clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream_obj)
-    for _ in range(args.steps):
+    for _ in range(steps):
         ctx.bege_batch_run(batch, stream)
     e1.record(stream_obj)
     torch.cuda.synchronize()
+    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     corr = sum(e.k1 - e.k0 for e in entries)
     flops = sum((e.k1 - e.k0) * metrics.nominal_flops_per_correlation(e.seg.n) for e in entries)
     tails = sum(ctx.bege_batch_fetch_tails(batch, i, capacity=0)[1] for i in range(len(entries)))
-    line = {
-        "form": "batch", "metric": "chirp correlations/s, batching form", "value":
-        corr * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": (f"{len(entries)} segments, N uniform over 2^14..2^17, sub-banks "
-                                "of 2^12..2^16 chirps (log-uniform), tau 0.5 or 1 s, 8 injections "
-                                "each, kappa 5.5"),
-                   "correlations_per_step": corr,
-                   "segment_lengths": sorted({e.seg.n for e in entries})},
-        "nominal_tflops": flops * args.steps / (ms / 1e3) / 1e12,
-        "plan": {"plan": ["persistent", "per-segment"][plan[0]], "chunk": plan[1],
-                 "order": ["longest-first", "interleaved"][plan[2]], "autotuned_ms": tuned_ms},
-        "tails_per_step": tails,
-    }
-    print(json.dumps(line), flush=True)
     ctx.close()
+    return {
+        "value": corr * steps / (ms / 1e3), "unit": UNIT, "graph_launches": steps,
+        "ms_per_graph_launch": ms / steps,
+        "workload": (f"{len(entries)} segments, N uniform over 2^14..2^17, sub-banks of "
+                     "2^12..2^16 chirps (log-uniform), tau 0.5 or 1 s, 8 injections each, "
+                     "kappa 5.5; one CUDA graph launch per step"),
+        "correlations_per_graph_launch": corr,
+        "segment_lengths": sorted({e.seg.n for e in entries}),
+        "nominal_tflops": flops * steps / (ms / 1e3) / 1e12,
+        "autotuned": {"plan": ["persistent", "per-segment"][plan[0]], "chunk": plan[1],
+                      "order": ["longest-first", "interleaved"][plan[2]],
+                      "radix": plan_radix(plan), "autotuned_ms": tuned_ms},
+        "tails_per_graph_launch": tails,
+        "clocks": clk,
+    }
+
+
+def plan_radix(plan) -> str:
+    """The column FFT plan the batch runs (the autotuner's radix axis)."""
+    return plan[3] if len(plan) > 3 else "16x16x16"
+
+
+def run_batch_form(args):
+    """``--form batch``: the batching form alone, as its own JSON line."""
+    import torch
+    from paper_1708_01609_gb300 import build
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    build()
+    b = batch_form(args)
+    line = {"form": "batch", "metric": "chirp correlations/s, batching form", "value": b["value"],
+            "unit": UNIT, "n_gpus": 1, "steps": b["graph_launches"], "warmup": args.warmup,
+            "ms_per_step": b["ms_per_graph_launch"], "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": b["workload"]}, "batch": b}
+    print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serve_form(args):
+def serving_form(args, device: int = 0) -> dict:
     """Serving form: two channels of band-limited noise emit 8, 16 and 32 s
     segments with Poisson arrivals at 2x real time; every request searches the
     resident 2^20-chirp bank at kappa 5.5 under a 120 GB device budget.
     Paced run: latency (p50/p99), throughput, real-time factor.  Saturated
-    run (every request submitted at once): capacity."""
+    run (every request submitted at once): capacity.  Clocks are sampled
+    during each run."""
     import threading
 
-    import torch
-    from paper_1708_01609_gb300 import binding, build
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA GPU")
-    build()
+    from paper_1708_01609_gb300 import binding
     budget = 120 * 10**9
-    ctx = binding.Context(0, tail_capacity=1 << 21, hbm_budget_bytes=budget)
+    ctx = binding.Context(device, tail_capacity=1 << 21, hbm_budget_bytes=budget)
     params = S.grid_paper()
     bank = ctx.bege_define_bank(params, tau=1.0, taper_frac=0.05)
     count = len(params)
@@ -635,6 +684,8 @@ def run_serve_form(args):
 
     def run(arrivals, paced):
         ids = [None] * len(arrivals)
+        clocks = ClockSampler(device)
+        clocks.start()
         t0 = time.monotonic()
 
         def feed():
@@ -653,6 +704,7 @@ def run_serve_form(args):
             ctx.bege_serve_wait(sv, rid)
             infos.append(ctx.bege_serve_info_get(sv, rid))
             ctx.bege_serve_forget(sv, rid)
+        clk = clocks.stop()
         lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
         span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
         data_s = sum(a.n for a in arrivals) / S.FS
@@ -665,24 +717,45 @@ def run_serve_form(args):
             "tails_per_request_mean": float(np.mean([i["n_tails"] for i in infos])),
             "tails_per_request_max": int(max(i["n_tails"] for i in infos)),
             "segment_lengths": sorted({a.n for a in arrivals}),
+            "offered_real_time_factor": (data_s / (max(a.t for a in arrivals) -
+                                                   min(a.t for a in arrivals)) / 2.0
+                                         if paced and len(arrivals) > 1 else None),
+            "clocks": clk,
         }
 
     paced = run(S.serving_stream(args.serve_requests, seed=2024, speed=2.0), paced=True)
     burst = run(S.serving_stream(args.serve_burst, seed=7, speed=2.0), paced=False)
     ctx.bege_serve_destroy(sv)
-    line = {
-        "form": "serve", "metric": "served p99 latency, 2x real time, 2^20-chirp bank",
-        "value": paced["p99_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": ("two channels of band-limited noise, 8/16/32 s segments, "
-                                "Poisson arrivals at 2x real time per channel, full 2^20 "
-                                "chirp bank per request, kappa 5.5, 120 GB device budget"),
-                   "streams": args.serve_streams, "slice_templates": args.serve_slice},
+    ctx.close()
+    return {
+        "metric": "served p99 latency, 2x real time, 2^20-chirp bank",
+        "p50_ms": paced["p50_ms"], "p99_ms": paced["p99_ms"],
+        "correlations_per_s": paced["correlations_per_s"],
+        "real_time_factor": paced["real_time_factor"],
+        "tails_per_request_mean": paced["tails_per_request_mean"],
+        "workload": ("two channels of band-limited noise, 8/16/32 s segments, Poisson "
+                     "arrivals at 2x real time per channel, full 2^20 chirp bank per "
+                     "request, kappa 5.5, 120 GB device budget"),
+        "streams": args.serve_streams, "slice_templates": args.serve_slice,
         "paced": paced,
         "saturated": burst,
     }
+
+
+def run_serve_form(args):
+    """``--form serve``: the serving form alone, as its own JSON line."""
+    import torch
+    from paper_1708_01609_gb300 import build
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    build()
+    sv = serving_form(args)
+    line = {"form": "serve", "metric": sv["metric"], "value": sv["p99_ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": sv["workload"], "streams": sv["streams"],
+                       "slice_templates": sv["slice_templates"]},
+            "serving": sv}
     print(json.dumps(line), flush=True)
-    ctx.close()
     return 0
 
 
@@ -708,6 +781,13 @@ def main():
                          "(column FFTs as split-operand tensor-core GEMMs)")
     ap.add_argument("--no-precision-form", action="store_true",
                     help="skip timing the BF16x3 / FP16x3 precision form beside the FP32 path")
+    ap.add_argument("--shard", action="store_true",
+                    help="split the bank over the ranks (one segment, strong scaling) instead "
+                         "of one replica per rank")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the paced serving run (about 80 s) in the default line")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batching form in the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-templates", type=int, default=8,

@@ -7,7 +7,8 @@ so N ranks split a bank into contiguous row ranges, search their own range
 with no collective on the data path, and rank 0 concatenates the tails.  If
 a rank fails, the ranges it had not finished are re-queued to the ranks that
 are still alive.  The compute step is a callable, so the same logic drives
-GPU ranks (libbege) and CPU ranks in tests.
+GPU ranks (``LibbegeShard``: libbege on the rank's own device, holding only
+the rank's own rows of the bank) and CPU ranks in tests.
 """
 from __future__ import annotations
 
@@ -25,6 +26,25 @@ def shard_ranges(count: int, world: int) -> list[tuple[int, int]]:
         out.append((k, k + n))
         k += n
     return out
+
+
+def deal(pending: list, alive: list[int]) -> dict:
+    """Deal the pending chunks (in row order) to the live ranks as
+    contiguous runs whose lengths differ by at most one, so that in the
+    first round each rank gets one contiguous range of the bank."""
+    out, i = {}, 0
+    for r, (a, b) in zip(alive, shard_ranges(len(pending), len(alive))):
+        out[r] = pending[a:b]
+        i = b
+    return out
+
+
+def first_range(count: int, chunk: int, world: int, rank: int) -> tuple[int, int]:
+    """Rows [begin, end) that ``run_sharded`` deals to ``rank`` in its first
+    round (all ranks alive): the rank's resident shard of the bank."""
+    pending = [(k, min(k + chunk, count)) for k in range(0, count, chunk)]
+    mine = deal(pending, list(range(world)))[rank]
+    return (mine[0][0], mine[-1][1]) if mine else (0, 0)
 
 
 def merge_tails(parts: list[np.ndarray]) -> np.ndarray:
@@ -92,11 +112,13 @@ def run_sharded(dist, compute, count: int, chunk: int, fail_rank: int | None = N
     ``compute(k0, k1)`` returns this rank's tail records for rows [k0, k1),
     or a pair (records, (snr, tmpl)) with the chunk's per-lag maximum
     (Eq. Ak over those rows, as bege_fetch_max returns it).  Chunks are
-    dealt round-robin; after every round the ranks exchange (on the host,
+    dealt as contiguous runs (``deal``); after every round the ranks exchange (on the host,
     via all_gather_object) which chunks they finished.  A rank that raises
     is treated as failed: it reports no more progress, and its unfinished
     chunks are dealt again to the survivors.  ``fail_rank`` / ``fail_after``
     make that rank fail after that many chunks (fault injection for tests).
+    In the first round rank r gets the contiguous rows ``first_range``
+    gives; re-dealt chunks go to the survivors as contiguous runs too.
     Returns the merged tails on rank 0 (None elsewhere) and the set of ranks
     that failed; with projections, also the merged per-lag maximum over the
     whole bank (every rank), from one all_reduce(MAX) of the packed keys.
@@ -110,10 +132,7 @@ def run_sharded(dist, compute, count: int, chunk: int, fail_rank: int | None = N
     done_here = 0
     dead = False
     while pending:
-        # deal the pending chunks round-robin over the live ranks
-        assign = {r: [] for r in alive}
-        for i, c in enumerate(pending):
-            assign[alive[i % len(alive)]].append(c)
+        assign = deal(pending, alive)
         finished, crashed = [], False
         if not dead and rank in assign:
             for c in assign[rank]:
@@ -155,3 +174,69 @@ def run_sharded(dist, compute, count: int, chunk: int, fail_rank: int | None = N
     key = torch.from_numpy(proj_key if proj_key is not None else np.zeros(n, np.int64))
     dist.all_reduce(key, op=dist.ReduceOp.MAX)
     return tails, failed, projection_from_key(key.numpy())
+
+
+class LibbegeShard:
+    """The compute step of ``run_sharded`` on a GPU rank: libbege searches
+    of one segment against rows [k0, k1) of a chirp bank.
+
+    The rank defines only its own rows ``own`` = [b0, b1) of the bank on the
+    device (its shard, resident for the whole search); a chunk outside them
+    -- one re-dealt from a failed rank -- is defined for that chunk alone and
+    released after it.  Every row runs the same kernels whatever bank it
+    sits in, so the gathered tails, sigma and per-lag maxima equal a
+    single-process search of the whole bank bitwise.  Records and
+    projections carry bank-wide template indices.
+
+    ctx: a binding.Context; seg: its segment handle; params: (K, 2) array of
+    (f0, fdot) for the whole bank; project: also return each chunk's per-lag
+    maximum (bege_correlate_max / bege_fetch_max).  A chunk whose tails
+    overflow the context's tail capacity raises RuntimeError (so
+    ``run_sharded`` treats the rank as failed rather than lose records).
+    """
+
+    def __init__(self, ctx, seg: int, n: int, params: np.ndarray, own: tuple[int, int],
+                 kappa: float, tau: float = 1.0, taper_frac: float = 0.05,
+                 project: bool = False, stream: int = 0):
+        self.ctx, self.seg, self.n = ctx, seg, n
+        self.params, self.kappa = np.asarray(params, dtype=np.float64), kappa
+        self.tau, self.taper, self.project, self.stream = tau, taper_frac, project, stream
+        self.own = own
+        self.bank = None
+        if own[1] > own[0]:
+            self.bank = ctx.bege_define_bank(self.params[own[0]:own[1]], tau=tau,
+                                             taper_frac=taper_frac, stream=stream)
+        self.sigma = {}   # chunk (k0, k1) -> sigma of its rows
+
+    def __call__(self, k0: int, k1: int):
+        ctx = self.ctx
+        if self.bank is not None and self.own[0] <= k0 and k1 <= self.own[1]:
+            bank, base, temp = self.bank, self.own[0], False
+        else:
+            bank = ctx.bege_define_bank(self.params[k0:k1], tau=self.tau,
+                                        taper_frac=self.taper, stream=self.stream)
+            base, temp = k0, True
+        try:
+            if self.project:
+                job = ctx.bege_correlate_max(self.seg, bank, k0 - base, k1 - base, self.kappa,
+                                             self.stream)
+            else:
+                job = ctx.bege_correlate(self.seg, bank, k0 - base, k1 - base, self.kappa,
+                                         self.stream)
+            recs, total = ctx.bege_fetch_tails(job)
+            if total != len(recs):
+                ctx.bege_release(job)
+                raise RuntimeError(f"rows [{k0}, {k1}): {total} tails overflow the capacity")
+            recs = recs.copy()
+            recs["tmpl"] += np.uint32(base)
+            self.sigma[(k0, k1)] = ctx.bege_get_sigma(job, k1 - k0)
+            proj = None
+            if self.project:
+                snr, tmpl = ctx.bege_fetch_max(job, self.n)
+                tmpl = np.where(tmpl >= 0, tmpl + base, -1).astype(np.int32)
+                proj = (snr, tmpl)
+            ctx.bege_release(job)
+        finally:
+            if temp:
+                ctx.bege_release(bank)
+        return recs if proj is None else (recs, proj)

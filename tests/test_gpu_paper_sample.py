@@ -5,7 +5,7 @@ path and on both tensor-core forms; sigma and the kappa = 5.5 tail sets as
 well.  The oracle runs in a spawn pool, one process per core.
 
 Bars: FP32 within 1e-5 sigma, sigma within 1e-6 relative; BF16x3 / FP16x3
-within 2e-3 sigma, sigma within 1e-3; tail sets identical except entries
+within 2e-3 sigma, sigma within 1e-5 relative; tail sets identical except entries
 within max(1e-3, tolerance) sigma of the threshold.  The errors found are
 printed (run with -s)."""
 import multiprocessing as mp
@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 STRIDE = 256
 CHUNK = 256
 KAPPA = 5.5
-FORMS = {0: ("FP32", 1e-5, 1e-6), 1: ("BF16x3", 2e-3, 1e-3), 2: ("FP16x3", 2e-3, 1e-3)}
+FORMS = {0: ("FP32", 1e-5, 1e-6), 1: ("BF16x3", 2e-3, 1e-5), 2: ("FP16x3", 2e-3, 1e-5)}
 
 _Y = None
 _P = None

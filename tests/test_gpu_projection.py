@@ -171,7 +171,7 @@ def test_linear_tails_match_oracle(prec):
     bank = O.chirp_bank(params, 4096.0, 4096, 0.05)
     rho, sig = oracle_rho(seg_data.y, bank)
     tol = 1e-5 if prec == 0 else 2e-3
-    assert np.max(np.abs(sg / sig - 1)) <= (1e-6 if prec == 0 else 1e-3)
+    assert np.max(np.abs(sg / sig - 1)) <= (1e-6 if prec == 0 else 1e-5)
     near = max(1e-3, tol)
     got = {(int(t), int(l)): float(v) for t, l, v in zip(recs["tmpl"], recs["lag"], recs["value"])}
     n_ref = 0
@@ -276,3 +276,70 @@ def test_two_channel_coincidences():
     assert len(rows) == len(ref_rows) > 0
     for name in ref_rows.dtype.names:
         assert np.array_equal(rows[name], ref_rows[name])
+
+
+def test_two_channel_search_matches_oracle():
+    """Sec. 5 end to end: two channels (independent band-limited noise, the
+    same chirp injected at the same offset in both, a second chirp in one
+    channel only), each searched on the GPU with the per-lag maximum, against
+    the oracle's own per-lag maxima of both channels (from FP64 rho and
+    sigma) and the oracle's simultaneous-hit analysis of those.  At every
+    lag the two sides keep the same template, except where the choice is not
+    fixed by the arithmetic: the lag's best value lies within the tolerance
+    of the threshold (a hit on one side only) or two templates' values lie
+    within twice the tolerance of each other (a near tie).  Kept values agree
+    within 1e-5; the coincidence lag sets differ only at such lags."""
+    params = S.grid_paper(16, 32)                    # 512 in-band chirps
+    n, kappa, tol = 1 << 16, 4.0, 1e-5
+    lag, k, k_one = 20000, 277, 90                 # k_one: injected in channel 0 only
+    sig_e = S.expected_filter_rms(n)
+    ys = []
+    for c in (0, 1):
+        y = S.inject(S.band_limited_noise(n, 950 + c).astype(np.float64),
+                     S.chirp_signal(*params[k], 4096), lag, 25.0 * sig_e)
+        if c == 0:
+            y = S.inject(y.astype(np.float64), S.chirp_signal(*params[k_one], 4096), 41000,
+                         20.0 * sig_e)
+        ys.append(y)
+    ctx = make_ctx(tail_capacity=1 << 22)
+    bid = ctx.bege_define_bank(params)
+    gpu = []
+    for y in ys:
+        seg = ctx.bege_load_segment(y)
+        job = ctx.bege_correlate_max(seg, bid, 0, len(params), kappa)
+        gpu.append(ctx.bege_fetch_max(job, n))
+    ctx.close()
+    bank = O.chirp_bank(params, 4096.0, 4096, 0.05)
+    undecided = np.zeros(n, bool)       # lags where the kept template is not fixed
+    orc = []
+    for (snr, tmpl), y in zip(gpu, ys):
+        rho, sig = oracle_rho(y, bank, batch=32)
+        val = rho / sig[:, None]
+        o_snr, o_tmpl = O.max_projection(rho, sig, kappa)
+        orc.append((o_snr, o_tmpl))
+        best = val.max(axis=0)
+        near_thr = np.abs(best - kappa) <= max(1e-3, 2 * tol)
+        second = np.partition(val, -2, axis=0)[-2]
+        tie = (best - second) <= 2 * tol
+        undecided |= near_thr | tie
+        same = (tmpl == o_tmpl)
+        assert np.all(same | near_thr | tie)
+        both = same & (tmpl >= 0)
+        assert both.sum() > 1000
+        assert np.all(np.abs(snr[both] - o_snr[both]) <= tol)
+        assert tmpl[lag] == o_tmpl[lag] >= 0
+    f0 = params[:, 0]
+    g = coincidences_of(gpu, f0)
+    o = O.coincidences(orc[0][1], orc[1][1], f0)
+    assert o["simultaneous"] > 10 and lag in o["lags"].tolist()
+    diff = np.setxor1d(g["lags"], o["lags"])
+    assert np.all(undecided[diff]), diff[~undecided[diff]]
+    assert abs(g["within_delta"] - o["within_delta"]) <= int(undecided.sum())
+    for c in (0, 1):
+        assert abs(g["hits"][c] - o["hits"][c]) <= int(undecided.sum())
+
+
+def coincidences_of(proj, f0):
+    from paper_1708_01609_gb300.output import coincidences
+    (_, t1), (_, t2) = proj
+    return coincidences(t1, t2, f0)

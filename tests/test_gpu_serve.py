@@ -1,14 +1,16 @@
 """Serving form: continuous batching over a resident bank.  Each request's
 result is the same alone and in a mix of concurrent requests (bitwise: every
 template runs the same kernel arithmetic), equals the regular entry points,
-and requests queue under a small HBM budget instead of failing."""
+matches the FP64 oracle on sampled templates, and requests queue under a
+small HBM budget instead of failing."""
 import time
 
 import numpy as np
 import pytest
 
+import oracle as O
 import synthetic as S
-from gpu_helpers import make_ctx
+from gpu_helpers import compare_tails, make_ctx, oracle_rho
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +24,7 @@ def served(request):
     ctx = make_ctx(tail_capacity=1 << 20, precision=request.param)
     params = S.grid_paper(64, 96)                     # 6144 in-band chirps
     bank = ctx.bege_define_bank(params, tau=1.0)
-    yield ctx, params, bank
+    yield ctx, params, bank, request.param
     ctx.close()
 
 
@@ -34,7 +36,7 @@ def result(ctx, sv, rid, count):
 
 
 def test_alone_equals_in_the_mix_and_regular_path(served):
-    ctx, params, bank = served
+    ctx, params, bank, _ = served
     count = len(params)
     reqs = S.serving_stream(9, seed=5, n_inject=2, params=params)
     sv = ctx.bege_serve_create(bank, KAPPA, streams=3, slice_templates=1000)
@@ -66,8 +68,47 @@ def test_alone_equals_in_the_mix_and_regular_path(served):
         ctx.bege_release(seg)
 
 
+def test_served_requests_match_oracle(served):
+    """Three requests of 8, 16 and 32 s from the two channels, each with two
+    injected chirps of the bank, served together (their slices interleave on
+    three streams): every request's sigma and tails on a sample of templates
+    (every injected template with its neighbours in f0 and fdot, and 16
+    random ones) against the FP64 oracle.  Bars as for the regular path:
+    sigma within 1e-6 relative (1e-5 for the precision form), tail values
+    within 1e-5 sigma (2e-3 sigma), tail sets identical away from the
+    threshold."""
+    ctx, params, bank, prec = served
+    count, n_f0 = len(params), 96
+    tol, sig_tol = (1e-5, 1e-6) if prec == 0 else (2e-3, 1e-5)
+    segs = [(c, S.make_segment(n, params, 2, 300 + i))
+            for i, (c, n) in enumerate([(0, 1 << 15), (1, 1 << 16), (0, 1 << 17)])]
+    sv = ctx.bege_serve_create(bank, KAPPA, streams=3, slice_templates=1000)
+    ids = [ctx.bege_serve_submit(sv, seg.y, c) for c, seg in segs]
+    served_out = [result(ctx, sv, rid, count) for rid in ids]
+    infos = [ctx.bege_serve_info_get(sv, rid) for rid in ids]
+    ctx.bege_serve_destroy(sv)
+    assert [i["n"] for i in infos] == [1 << 15, 1 << 16, 1 << 17]
+    rng = np.random.Generator(np.random.PCG64(77))
+    for (c, seg), (recs, sig) in zip(segs, served_out):
+        sample = set(rng.choice(count, 16, replace=False).tolist())
+        for k, _, _ in seg.injections:
+            for d in (0, -1, 1, -n_f0, n_f0):
+                if 0 <= k + d < count:
+                    sample.add(k + d)
+        sample = sorted(sample)
+        bank64 = O.chirp_bank(params[sample], 4096.0, 4096, 0.05)
+        rho, osig = oracle_rho(seg.y, bank64)
+        assert np.all(np.abs(sig[sample] / osig - 1) <= sig_tol)
+        res = compare_tails(recs, {k: (rho[i], osig[i]) for i, k in enumerate(sample)},
+                            KAPPA, tmpl_subset=sample, tol=tol)
+        assert res["matched"] > 0
+        got = set(zip(recs["tmpl"].tolist(), recs["lag"].tolist()))
+        for k, lag, _ in seg.injections:
+            assert (k, lag) in got, (seg.n, k, lag)
+
+
 def test_budget_admission_queues_requests(served):
-    ctx, params, bank = served
+    ctx, params, bank, _ = served
     count = len(params)
     reqs = S.serving_stream(6, seed=8)
     # room for one 32 s segment's spectrum at a time

@@ -2,7 +2,9 @@
 operands (BF16x3, FP16x3) and FP32 accumulation, against the FP64 oracle.
 
 Bar for the reduced-precision path: correlation values within 2e-3 sigma of
-the oracle; sigma within 1e-3 relative; tail sets identical except entries
+the oracle; sigma within 1e-5 relative (sigma is an FP32 sum over the
+spectrum, whose split-precision error is near 1e-6 relative, so 1e-5 leaves
+a margin of about five); tail sets identical except entries
 within the value tolerance (2e-3 sigma) of the threshold.  The errors found
 are printed (run with -s to see them).
 """
@@ -16,6 +18,7 @@ from gpu_helpers import compare_tails, make_ctx, oracle_rho
 pytestmark = pytest.mark.gpu
 
 TOL_TC = 2e-3
+TOL_SIGMA_TC = 1e-5
 PRECISIONS = {1: "BF16x3", 2: "FP16x3"}
 
 
@@ -46,7 +49,7 @@ def test_tc_dump_matches_oracle(tctx, n, length):
     print(f"{PRECISIONS[prec]} N={n} L={length}: max|err| {err.max():.2e} sigma, "
           f"rms {rms.max():.2e} sigma, sigma rel err {serr:.2e}")
     assert np.all(err <= TOL_TC), err
-    assert serr <= 1e-3
+    assert serr <= TOL_SIGMA_TC
     for h in (job, bid, seg):
         ctx.bege_release(h)
 
@@ -138,7 +141,7 @@ def test_tc_paper_scale_tails_match_fp32_path(prec):
         ctx.close()
     (k32, v32), sig32 = out[0]
     (ktc, vtc), sigtc = out[prec]
-    assert np.max(np.abs(sigtc / sig32 - 1)) <= 1e-3
+    assert np.max(np.abs(sigtc / sig32 - 1)) <= TOL_SIGMA_TC
     both, i32, itc = np.intersect1d(k32, ktc, assume_unique=True, return_indices=True)
     tmpl = (both >> 32).astype(np.int64)
     err = np.abs(v32[i32] - vtc[itc]) / sig32[tmpl]

@@ -171,3 +171,20 @@ def test_sharded_search_merges_projections(tmp_path, fail_rank):
     assert np.array_equal(m_snr, snr.astype(np.float32))
     assert n_tails == len(res["tails"])
     assert n_failed == (0 if fail_rank is None else 1)
+
+
+def test_deal_gives_contiguous_runs():
+    pending = [(k, min(k + 3, 20)) for k in range(0, 20, 3)]   # 7 chunks
+    a = shard.deal(pending, [0, 1])
+    assert a[0] == pending[:4] and a[1] == pending[4:]
+    b = shard.deal(pending[2:], [1])
+    assert b[1] == pending[2:]
+    assert shard.first_range(20, 3, 2, 0) == (0, 12)
+    assert shard.first_range(20, 3, 2, 1) == (12, 20)
+    assert shard.first_range(2, 3, 2, 1) == (0, 0)
+    # every row is dealt exactly once
+    for count, chunk, world in [(65536, 8192, 2), (1000, 7, 3), (5, 10, 4)]:
+        got = [shard.first_range(count, chunk, world, r) for r in range(world)]
+        cover = sorted(x for x in got if x[1] > x[0])
+        assert cover[0][0] == 0 and cover[-1][1] == count
+        assert all(p[1] == q[0] for p, q in zip(cover, cover[1:]))
