@@ -336,6 +336,15 @@ __device__ __forceinline__ PairItem pair_item(int ug, int ui, int it) {
   return p;
 }
 
+// Y = conj(x) A + y B with ab = {A, B}: the spectral product of Eq. 3S in
+// the packed form.  (Written as two chains of fused multiply-adds it needs
+// two instructions fewer per value, but the longer chains make the fused
+// middle stage spill.)
+__device__ __forceinline__ float2 packed_product(float2 x, float2 y, float4 ab) {
+  const float2 xa = make_float2(fmaf(x.x, ab.x, x.y * ab.y), fmaf(x.x, ab.y, -x.y * ab.x));
+  return cadd(xa, cmul(y, make_float2(ab.z, ab.w)));
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -439,8 +448,8 @@ __device__ __forceinline__ float fused_mid(int rank, const float4* __restrict__ 
         const float4 p = __ldcg(aba + 256 * r);
         const float4 q = __ldcg(abb + 256 * (15 - r));
         const float2 x = za[r], y = zb[15 - r];
-        const float2 ya = cadd(cconjmul(x, make_float2(p.x, p.y)), cmul(y, make_float2(p.z, p.w)));
-        const float2 yb = cadd(cconjmul(y, make_float2(q.x, q.y)), cmul(x, make_float2(q.z, q.w)));
+        const float2 ya = packed_product(x, y, p);
+        const float2 yb = packed_product(y, x, q);
         acc = fmaf(ya.x, ya.x, fmaf(ya.y, ya.y, acc));
         acc = fmaf(yb.x, yb.x, fmaf(yb.y, yb.y, acc));
         za[r] = ya;
@@ -453,14 +462,14 @@ __device__ __forceinline__ float fused_mid(int rank, const float4* __restrict__ 
       for (int r = 0; r < 16; ++r) {
         const int rp = (16 - r) & 15;
         const float4 p = __ldcg(aba + 256 * r);
-        ya[r] = cadd(cconjmul(za[r], make_float2(p.x, p.y)), cmul(za[rp], make_float2(p.z, p.w)));
+        ya[r] = packed_product(za[r], za[rp], p);
         acc = fmaf(ya[r].x, ya[r].x, fmaf(ya[r].y, ya[r].y, acc));
       }
       // butterfly 128: rows 128 + 256 r pair with 128 + 256 (15 - r)
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         const float4 q = __ldcg(abb + 256 * r);
-        yb[r] = cadd(cconjmul(zb[r], make_float2(q.x, q.y)), cmul(zb[15 - r], make_float2(q.z, q.w)));
+        yb[r] = packed_product(zb[r], zb[15 - r], q);
         acc = fmaf(yb[r].x, yb[r].x, fmaf(yb[r].y, yb[r].y, acc));
       }
 #pragma unroll
@@ -726,12 +735,10 @@ __device__ __forceinline__ void template_columns(int grank, const float* __restr
         const float4 abj = __ldcg(AB + q.b * F + q.a);
         const float4 abp = __ldcg(AB + q.bp * F + q.ap);
         const float2 zj = *cj, zp = *cp;
-        const float2 yj = cadd(cconjmul(zj, make_float2(abj.x, abj.y)),
-                               cmul(zp, make_float2(abj.z, abj.w)));
+        const float2 yj = packed_product(zj, zp, abj);
         acc = fmaf(yj.x, yj.x, fmaf(yj.y, yj.y, acc));
         if (cj != cp) {
-          const float2 yp = cadd(cconjmul(zp, make_float2(abp.x, abp.y)),
-                                 cmul(zj, make_float2(abp.z, abp.w)));
+          const float2 yp = packed_product(zp, zj, abp);
           acc = fmaf(yp.x, yp.x, fmaf(yp.y, yp.y, acc));
           *cp = yp;
         }

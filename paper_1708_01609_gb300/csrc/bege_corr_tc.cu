@@ -12,22 +12,42 @@ __device__ __forceinline__ void group_sync(int g) {
 
 // GEMM step of group g: operand writes are made visible to the tensor cores,
 // the group synchronises, its first thread issues the MMAs and every thread
-// waits (bounded) on the group's mbarrier.  Returns false if the wait gave up.
+// waits (bounded) on the group's mbarrier.
+//
+// Give-up path: a thread whose wait gives up clears `ok` and keeps `parity`
+// at the phase it gave up on.  From then on it waits no more, and if it is
+// the issuing thread it issues no more MMAs, so the commit of that phase is
+// the only one that can still be pending (every earlier phase was waited
+// for).  The kernel keeps its barriers in step with the cluster, finishes its
+// loop with meaningless values, reports the failure in the job's status word
+// and, before releasing tensor memory, the issuing thread waits once more for
+// the phase it gave up on (drain_after_give_up).
 template <int P>
-__device__ __forceinline__ bool gemm(int g, int lt, uint32_t tmem, uint32_t ah, uint32_t al,
+__device__ __forceinline__ void gemm(int g, int lt, uint32_t tmem, uint32_t ah, uint32_t al,
                                      uint32_t bh, uint32_t bl, bool a_mn, int K, uint32_t mbar,
-                                     uint32_t& parity) {
+                                     uint32_t& parity, bool& ok) {
   asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   group_sync(g);
-  if (lt == 0) {
+  if (lt == 0 && ok) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     issue_gemm<P>(tmem, ah, al, bh, bl, a_mn, K, mbar);
   }
-  const bool ok = mbar_wait(mbar, parity);
-  parity ^= 1u;
+  if (ok) {
+    if (mbar_wait(mbar, parity))
+      parity ^= 1u;
+    else
+      ok = false;
+  }
   asm volatile("tcgen05.fence::after_thread_sync;");
-  return ok;
+}
+
+// Before tensor memory is released: if the issuing thread gave up on a
+// phase, its commit may still be pending; wait for it once more (bounded).
+// Whatever the outcome the failure is already in the job's status word.
+__device__ __forceinline__ void drain_after_give_up(int lt, bool ok, uint32_t mbar,
+                                                    uint32_t parity) {
+  if (lt == 0 && !ok) (void)mbar_wait(mbar, parity);
 }
 
 // Half the accumulator row of this thread, in two chunks q = 0, 1: warp w of
@@ -236,9 +256,9 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
       store_split8<P>(a_hi, a_lo, off_kmajor(row, kperm(0, 8 * blk)), ure[i]);
       store_split8<P>(a_hi, a_lo, off_kmajor(row, kperm(1, 8 * blk)), uim[i]);
     }
-    ok &= gemm<P>(g, lt, tmem, ah, al, bh, bl, false, 64, mbar, parity);  // inputs m2 < 32 only
+    gemm<P>(g, lt, tmem, ah, al, bh, bl, false, 64, mbar, parity, ok);  // m2 < 32 only
     twiddle_to_mn<P, G>(tmem, a_hi, a_lo);
-    ok &= gemm<P>(g, lt, tmem, ah, al, bh, bl, true, 128, mbar, parity);
+    gemm<P>(g, lt, tmem, ah, al, bh, bl, true, 128, mbar, parity, ok);
     {  // Z[c][k1 + 64 k2] to the FP32 staging columns (the A operand is dead)
       float2* col = SM::col(tslot_);
       const float inv = 1.0f / su;  // exact: su is a power of two
@@ -277,10 +297,8 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int it = it0 + u * kGT + lt, ip = kF - 1 - it;
-          const float2 yj = cadd(cconjmul(zj[u], make_float2(abj[u].x, abj[u].y)),
-                                 cmul(zp[u], make_float2(abj[u].z, abj[u].w)));
-          const float2 yp = cadd(cconjmul(zp[u], make_float2(abp[u].x, abp[u].y)),
-                                 cmul(zj[u], make_float2(abp[u].z, abp[u].w)));
+          const float2 yj = packed_product(zj[u], zp[u], abj[u]);
+          const float2 yp = packed_product(zp[u], zj[u], abp[u]);
           acc = fmaf(yj.x, yj.x, fmaf(yj.y, yj.y, acc));
           acc = fmaf(yp.x, yp.x, fmaf(yp.y, yp.y, acc));
           ymax = fmaxf(ymax, fmaxf(fmaxf(fabsf(yj.x), fabsf(yj.y)), fmaxf(fabsf(yp.x), fabsf(yp.y))));
@@ -312,13 +330,11 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if (oj[u] < 0) continue;
-          const float2 yj = cadd(cconjmul(zj[u], make_float2(abj[u].x, abj[u].y)),
-                                 cmul(zp[u], make_float2(abj[u].z, abj[u].w)));
+          const float2 yj = packed_product(zj[u], zp[u], abj[u]);
           acc = fmaf(yj.x, yj.x, fmaf(yj.y, yj.y, acc));
           ymax = fmaxf(ymax, fmaxf(fabsf(yj.x), fabsf(yj.y)));
           if (oj[u] != op[u]) {
-            const float2 yp = cadd(cconjmul(zp[u], make_float2(abp[u].x, abp[u].y)),
-                                   cmul(zj[u], make_float2(abp[u].z, abp[u].w)));
+            const float2 yp = packed_product(zp[u], zj[u], abp[u]);
             acc = fmaf(yp.x, yp.x, fmaf(yp.y, yp.y, acc));
             ymax = fmaxf(ymax, fmaxf(fabsf(yp.x), fabsf(yp.y)));
             SM::col(0)[op[u]] = yp;
@@ -366,9 +382,9 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
         store_split8<P>(a_hi, a_lo, off_kmajor(row, kperm(1, 8 * blk)), yim[i]);
       }
     }
-    ok &= gemm<P>(g, lt, tmem, ah, al, bh, bl, false, 128, mbar, parity);
+    gemm<P>(g, lt, tmem, ah, al, bh, bl, false, 128, mbar, parity, ok);
     twiddle_to_mn<P, G>(tmem, a_hi, a_lo);
-    ok &= gemm<P>(g, lt, tmem, ah, al, bh, bl, true, 128, mbar, parity);
+    gemm<P>(g, lt, tmem, ah, al, bh, bl, true, 128, mbar, parity, ok);
     {  // T_b[n1] = wH^(-b n1) conj(D), n1 = n1a + 64 n1b, to the staging columns
       const float2 ta = SM::tin_a()[ttab * 64 + tr];
       const float2 step = SM::tin_b()[ttab * 64 + 1];
@@ -419,6 +435,7 @@ __global__ void __launch_bounds__(kGT * G, 1) correlate_tc_kernel(PlanDev p, Cor
   }
 
   if (!ok && a.status) atomicOr(a.status, 1u);
+  drain_after_give_up(lt, ok, mbar, parity);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot),

@@ -26,25 +26,44 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
-// conj(a) * b
-__device__ __forceinline__ float2 cconjmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
-}
 // multiply by -i (forward) or +i (inverse)
 template <bool INV>
 __device__ __forceinline__ float2 mul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
-// multiply by exp(-i t) (forward) or exp(+i t) (inverse), with c = cos t, s = sin t
-template <bool INV>
-__device__ __forceinline__ float2 twc(float2 a, float c, float s) {
-  return INV ? make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.y, c, a.x * s))
-             : make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
-}
 
 constexpr float kC1 = 0.92387953251128674f;  // cos(pi/8)
 constexpr float kS1 = 0.38268343236508978f;  // sin(pi/8)
 constexpr float kR2 = 0.70710678118654752f;  // cos(pi/4)
+constexpr float kT1 = 0.41421356237309505f;  // tan(pi/8)
+
+// Twiddles in factored form, so that a twiddle multiply and the addition
+// that follows it become fused multiply-adds (the tangent form of a
+// rotation: exp(-i a) = cos a (1 - i tan a)).  rot_a multiplies by
+// (1 - i t) in the forward direction and (1 + i t) in the inverse one (the
+// direction of w16 = exp(-i pi/8) and of its conjugate); rot_b the opposite.
+template <bool INV>
+__device__ __forceinline__ float2 rot_a(float2 q, float t) {
+  return INV ? make_float2(fmaf(-t, q.y, q.x), fmaf(t, q.x, q.y))
+             : make_float2(fmaf(t, q.y, q.x), fmaf(-t, q.x, q.y));
+}
+template <bool INV>
+__device__ __forceinline__ float2 rot_b(float2 q, float t) {
+  return rot_a<!INV>(q, t);
+}
+// t = 1: (1 -/+ i) q with two additions
+template <bool INV>
+__device__ __forceinline__ float2 rot_a1(float2 q) {
+  return INV ? make_float2(q.x - q.y, q.y + q.x) : make_float2(q.x + q.y, q.y - q.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 rot_b1(float2 q) {
+  return rot_a1<!INV>(q);
+}
+// p + s u, componentwise
+__device__ __forceinline__ float2 cfma(float2 p, float s, float2 u) {
+  return make_float2(fmaf(s, u.x, p.x), fmaf(s, u.y, p.y));
+}
 
 template <bool INV>
 __device__ __forceinline__ void dft2(float2& a, float2& b) {
@@ -64,19 +83,58 @@ __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2&
   x3 = csub(d02, d13);
 }
 
+// DFT4 of (x0, w x1, w^2 x2, w^3 x3) with w = w16^K1 (forward) or its
+// conjugate (inverse), in place, natural order out.  With a = x0 + w^2 x2,
+// b = x0 - w^2 x2, c = x1 + w^2 x3, d = x1 - w^2 x3 the outputs are
+// a + w c, b + m(w d), a - w c, b - m(w d), m = multiplication by -i
+// (forward) or +i (inverse); each twiddle enters through the tangent form,
+// so a twiddle multiply and its addition cost two fused multiply-adds.
+template <bool INV, int K1>
+__device__ __forceinline__ void dft4_tw16(float2& x0, float2& x1, float2& x2, float2& x3) {
+  float2 a, b, c, d;
+  if constexpr (K1 == 0) {
+    dft4<INV>(x0, x1, x2, x3);
+    return;
+  } else if constexpr (K1 == 1) {  // w^2 = w8 = r2 (1 -/+ i)
+    const float2 u2 = rot_a1<INV>(x2), u3 = rot_a1<INV>(x3);
+    a = cfma(x0, kR2, u2); b = cfma(x0, -kR2, u2);
+    c = cfma(x1, kR2, u3); d = cfma(x1, -kR2, u3);
+    // w = c1 (1 -/+ i t1)
+    const float2 vc = rot_a<INV>(c, kT1), vd = mul_mi<INV>(rot_a<INV>(d, kT1));
+    x0 = cfma(a, kC1, vc); x2 = cfma(a, -kC1, vc);
+    x1 = cfma(b, kC1, vd); x3 = cfma(b, -kC1, vd);
+  } else if constexpr (K1 == 2) {  // w^2 = w4 = m, w = w8 = r2 (1 -/+ i)
+    const float2 m2 = mul_mi<INV>(x2), m3 = mul_mi<INV>(x3);
+    a = cadd(x0, m2); b = csub(x0, m2);
+    c = cadd(x1, m3); d = csub(x1, m3);
+    const float2 uc = rot_a1<INV>(c), ud = mul_mi<INV>(rot_a1<INV>(d));
+    x0 = cfma(a, kR2, uc); x2 = cfma(a, -kR2, uc);
+    x1 = cfma(b, kR2, ud); x3 = cfma(b, -kR2, ud);
+  } else {  // K1 == 3: w^2 = w8^3 = -r2 (1 +/- i), w = w16^3 = m(c1 (1 +/- i t1))
+    static_assert(K1 == 3, "twiddle index");
+    const float2 u2 = rot_b1<INV>(x2), u3 = rot_b1<INV>(x3);
+    a = cfma(x0, -kR2, u2); b = cfma(x0, kR2, u2);
+    c = cfma(x1, -kR2, u3); d = cfma(x1, kR2, u3);
+    // w c = m(c1 vc); m(w d) = m(m(c1 vd)) = -c1 vd
+    const float2 vc = mul_mi<INV>(rot_b<INV>(c, kT1)), vd = rot_b<INV>(d, kT1);
+    x0 = cfma(a, kC1, vc); x2 = cfma(a, -kC1, vc);
+    x1 = cfma(b, -kC1, vd); x3 = cfma(b, kC1, vd);
+  }
+}
+
 template <bool INV>
 __device__ __forceinline__ void dft8(float2 (&x)[8]) {
   float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
   float2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
   dft4<INV>(e0, e1, e2, e3);
   dft4<INV>(o0, o1, o2, o3);
-  o1 = twc<INV>(o1, kR2, kR2);    // w8^1
-  o2 = mul_mi<INV>(o2);           // w8^2
-  o3 = twc<INV>(o3, -kR2, kR2);   // w8^3
+  // e_k +/- w8^k o_k: w8 = r2 (1 -/+ i), w8^2 = m, w8^3 = -r2 (1 +/- i)
+  const float2 u1 = rot_a1<INV>(o1), u3 = rot_b1<INV>(o3);
+  o2 = mul_mi<INV>(o2);
   x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
-  x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
+  x[1] = cfma(e1, kR2, u1); x[5] = cfma(e1, -kR2, u1);
   x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
-  x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
+  x[3] = cfma(e3, -kR2, u3); x[7] = cfma(e3, kR2, u3);
 }
 
 // 16 = 4 x 4: DFT4 over the stride-4 index, twiddle w16^(n2 k1), DFT4 over
@@ -97,18 +155,11 @@ __device__ __forceinline__ void dft16(float2 (&x)[16]) {
       dft4<INV>(x[n2], x[n2 + 4], x[n2 + 8], x[n2 + 12]);
     }
   }
-  // x[n2 + 4 k1] *= w16^(n2 k1)
-  x[5] = twc<INV>(x[5], kC1, kS1);     // m = 1
-  x[6] = twc<INV>(x[6], kR2, kR2);     // m = 2
-  x[7] = twc<INV>(x[7], kS1, kC1);     // m = 3
-  x[9] = twc<INV>(x[9], kR2, kR2);     // m = 2
-  x[10] = mul_mi<INV>(x[10]);          // m = 4
-  x[11] = twc<INV>(x[11], -kR2, kR2);  // m = 6
-  x[13] = twc<INV>(x[13], kS1, kC1);   // m = 3
-  x[14] = twc<INV>(x[14], -kR2, kR2);  // m = 6
-  x[15] = twc<INV>(x[15], -kC1, -kS1); // m = 9
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+  // DFT4 over n2 of x[n2 + 4 k1] w16^(n2 k1), the twiddles merged into it
+  dft4_tw16<INV, 0>(x[0], x[1], x[2], x[3]);
+  dft4_tw16<INV, 1>(x[4], x[5], x[6], x[7]);
+  dft4_tw16<INV, 2>(x[8], x[9], x[10], x[11]);
+  dft4_tw16<INV, 3>(x[12], x[13], x[14], x[15]);
   float2 t[16];
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1)
