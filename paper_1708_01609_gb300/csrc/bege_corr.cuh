@@ -587,7 +587,11 @@ struct TailOut {
 // end a.kappa_hi and the lag mask a.lag_end (compiled only into the kernels
 // that serve bege_correlate_max, bege_correlate_band and bege_correlate_ex,
 // so the others keep their code unchanged).  sigma: the template's sigma (thr = kappa sigma).
-template <int F, int S, int NC, int T, bool EXT = false>
+//
+// IL: the columns are interleaved two per CTA (NC = 2); `colptr` then holds
+// the C CTAs' row arrays (float4*, cast), CTA u holding columns u and S - u
+// (CTA 0: 0 and S/2), and a row of both comes in one 16-byte load.
+template <int F, int S, int NC, int T, bool EXT = false, bool IL = false>
 __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, int rank, float thr,
                                                  uint32_t tmpl, int64_t krow, const TailOut& a,
                                                  float sigma, int tix = threadIdx.x) {
@@ -606,8 +610,18 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
     const int n1 = rank * per + it * T + tix;
     const int pn1 = pad(n1);
     float2 t[S];
+    if constexpr (IL) {
+      static_assert(NC == 2 && S >= 2, "interleaved columns: one unit per CTA");
 #pragma unroll
-    for (int b = 0; b < S; ++b) t[b] = colptr[b][pn1];
+      for (int u = 0; u < S / 2; ++u) {
+        const float4 v = reinterpret_cast<const float4*>(colptr[u])[pn1];
+        t[u] = make_float2(v.x, v.y);
+        t[u == 0 ? S / 2 : S - u] = make_float2(v.z, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < S; ++b) t[b] = colptr[b][pn1];
+    }
     dft<S, true>(t);
     float big = 0.f;
 #pragma unroll
@@ -672,6 +686,143 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Interleaved columns (F = 4096, NC = 2, 256 threads, HALFZ templates).
+// Row i of the CTA's two columns is the float4 {slot 0 [i], slot 1 [i]} at
+// padded row index pad(i) (the same bytes as two separate padded columns).
+// In these passes a thread owns butterfly j of both columns, so a pass is
+// one round: every load before its barrier, every store after it.  A pass
+// can therefore also change the layout, and an interleaved row moves with
+// one 16-byte access; a Stockham twiddle (a function of the row, not of the
+// column) is loaded once for both columns.  The forward passes end in the
+// separate layout, where the fused middle's mirror accesses are free of bank
+// conflicts; the inverse passes end interleaved, so the combine reads a
+// unit's two columns with one load.  Every value sees the same arithmetic
+// in the same order as in the separate layout, and the fused middle keeps
+// its thread-to-item map, so the results are bitwise the same.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4* il_rows() { return reinterpret_cast<float4*>(smem_raw); }
+__device__ __forceinline__ float4 il_pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// Row loads and stores of both columns at padded row index i: interleaved
+// (IL, one 16-byte access) or from the two separate columns.
+template <bool IL>
+__device__ __forceinline__ void il_load(int i, float2& a, float2& b) {
+  if constexpr (IL) {
+    const float4 v = il_rows()[i];
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+  } else {
+    a = Smem<4096, 2>::col(0)[i];
+    b = Smem<4096, 2>::col(1)[i];
+  }
+}
+template <bool IL>
+__device__ __forceinline__ void il_store(int i, float2 a, float2 b) {
+  if constexpr (IL) {
+    il_rows()[i] = il_pack(a, b);
+  } else {
+    Smem<4096, 2>::col(0)[i] = a;
+    Smem<4096, 2>::col(1)[i] = b;
+  }
+}
+
+// First forward pass (radix 16, Ns = 1) of both columns from the template's
+// nz <= F/2 complex samples: u_c[m1] = wH^(b_c m1) z[m1], upper half zero.
+template <bool OUT_IL>
+__device__ __forceinline__ void il_fwd_first_pass(const float* __restrict__ src, int nz) {
+  using SM = Smem<4096, 2>;
+  const float2* z = reinterpret_cast<const float2*>(src);
+  const int j = threadIdx.x;
+  float2 va[16], vb[16];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int m1 = j + r * 256;
+    va[r] = vb[r] = m1 < nz ? __ldg(z + m1) : make_float2(0.f, 0.f);
+  }
+  const float2 ta = SM::twin()[j], tb = SM::twin()[256 + j];
+  const float2* ra = SM::rin();
+  const float2* rb = SM::rin() + 16;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    va[r] = cmul(cmul(va[r], ta), ra[r]);
+    vb[r] = cmul(cmul(vb[r], tb), rb[r]);
+  }
+  dft<16, false, true>(va);
+  dft<16, false, true>(vb);
+  const int q = pad(16 * j);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) il_store<OUT_IL>(q + r, va[r], vb[r]);
+  __syncthreads();
+}
+
+// One radix-16 Stockham pass (NB = 256 butterflies per column, Ns = NS) of
+// both columns, in one round: every load before the barrier, every store
+// after it, so the pass may also change the layout (IN_IL -> OUT_IL).
+// Ends with a barrier.
+template <int NS, bool INV, bool IN_IL, bool OUT_IL>
+__device__ __forceinline__ void il_pass(const float2* tw) {
+  constexpr int step = 256 + 16;  // padded distance of rows j + 256 r
+  static_assert(NS % 16 == 0, "strided stores");
+  const int j = threadIdx.x;
+  const int k = j & (NS - 1);
+  float2 va[16], vb[16];
+  const int p = pad(j);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) il_load<IN_IL>(p + r * step, va[r], vb[r]);
+  const float2* t = tw + k;
+#pragma unroll
+  for (int r = 1; r < 16; ++r) {
+    const float2 w = t[r * NS];
+    va[r] = INV ? cmulc(va[r], w) : cmul(va[r], w);
+    vb[r] = INV ? cmulc(vb[r], w) : cmul(vb[r], w);
+  }
+  dft<16, INV>(va);
+  dft<16, INV>(vb);
+  __syncthreads();
+  const int q = pad((j - k) * 16 + k);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) il_store<OUT_IL>(q + r * (NS + NS / 16), va[r], vb[r]);
+  __syncthreads();
+}
+
+// Last inverse pass (radix 16, Ns = F/16) of both columns with the output
+// twiddle T_b[n1] = wH^(-b n1) x[n1] (as inv_last_pass), in one round;
+// writes the interleaved layout.  TRAIL: end with a barrier.
+template <int S, bool IN_IL, bool TRAIL>
+__device__ __forceinline__ void il_inv_last_pass() {
+  using SM = Smem<4096, 2>;
+  constexpr int Ns = 256, step = 256 + 16;
+  const int j = threadIdx.x;
+  float2 va[16], vb[16];
+  const int p = pad(j);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) il_load<IN_IL>(p + r * step, va[r], vb[r]);
+  const float2* t3 = SM::tw3() + j;
+#pragma unroll
+  for (int r = 1; r < 16; ++r) {
+    const float2 w = t3[r * Ns];
+    va[r] = cmulc(va[r], w);
+    vb[r] = cmulc(vb[r], w);
+  }
+  dft<16, true>(va);
+  dft<16, true>(vb);
+  {
+    const float2 ta = SM::twin()[j], tb = SM::twin()[256 + j];
+    const float2* ra = SM::rout();
+    const float2* rb = SM::rout() + 16;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      va[r] = cmul(cmulc(va[r], ta), ra[r]);
+      vb[r] = cmul(cmulc(vb[r], tb), rb[r]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) il_store<true>(p + r * step, va[r], vb[r]);
+  if constexpr (TRAIL) __syncthreads();
+}
+
 // The CTA's share of sum |Y|^2: in its sigpart slot, and with SIGPUSH also
 // in slot grank of every CTA's sigall array.
 template <int F, int S, int NC, bool SIGPUSH>
@@ -694,14 +845,32 @@ __device__ __forceinline__ void store_sigma_partial(int grank, float s) {
 // sigall array, so each CTA sums the cluster's partials from its own memory
 // after the next cluster barrier (slot q is rewritten only after the
 // barrier that follows every CTA's read of it).
-template <int F, int S, int NC, int T, bool HALFZ, bool SIGPUSH = false>
+//
+// IL: interleaved columns (F = 4096, NC = 2, T = 256, HALFZ, S >= 2 only).
+template <int F, int S, int NC, int T, bool HALFZ, bool SIGPUSH = false, bool IL = false>
 __device__ __forceinline__ void template_columns(int grank, const float* __restrict__ src, int nz,
                                                  int nfold, const float4* __restrict__ AB,
                                                  int s_rt = S) {
   using SM = Smem<F, NC>;
   constexpr int UPC = S == 1 ? 1 : NC / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if constexpr (F == 4096) {
+  if constexpr (IL) {
+    static_assert(F == 4096 && NC == 2 && T == 256 && HALFZ && S != 1, "interleaved shape");
+    // the forward passes end in the separate layout (the fused middle's
+    // mirror accesses are conflict-free there); the inverse passes write
+    // the interleaved one, which the combine reads a row at a time
+    il_fwd_first_pass<true>(src, nz);
+    il_pass<16, false, true, false>(SM::tw2());
+    fused_mid<S, NC, T>(grank, AB, SM::red(), s_rt);
+    if (threadIdx.x == 0) {
+      float s = 0.f;
+      for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
+      store_sigma_partial<F, S, NC, SIGPUSH>(grank, s);
+    }
+    __syncthreads();
+    il_pass<16, true, false, true>(SM::tw2());
+    il_inv_last_pass<S, true, !SIGPUSH>();  // without it, a cluster barrier follows
+  } else if constexpr (F == 4096) {
     // S2: forward passes 1-2; S2-S5 fused: forward pass 3, the product
     // Y = conj(Z) A + Z' B with sum |Y|^2, inverse pass 1; S5: passes 2-3
     fwd_first_pass<F, S, NC, T, HALFZ>(grank, src, nz, nfold, s_rt);
@@ -790,14 +959,22 @@ __device__ __forceinline__ void cluster_sync_after_reads() {
                "memory");
 }
 
-template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool EXT>
+//
+// IL: the CTA's two columns interleaved (F = 4096, NC = 2, T = 256, HALFZ,
+// S >= 2); the results are the same bit for bit.
+template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool EXT, bool IL = false>
 __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, CorrelateArgs a) {
   constexpr int C = ColMap<S, NC>::C;
   cg::cluster_group cluster = cg::this_cluster();
   const int N = p.g.N, H = p.g.H;
   const int rank = (int)cluster.block_rank();
   setup_common<F, NC, T>(p);
-  setup_columns<F, S, NC, T>(p, rank, 0, true);
+  setup_columns<F, S, NC, T>(p, rank, 0, !IL);
+  if constexpr (IL) {  // the C CTAs' row arrays, for the combine
+    if (threadIdx.x < C)
+      Smem<F, NC>::colptr()[threadIdx.x] =
+          reinterpret_cast<float2*>(cluster.map_shared_rank(il_rows(), (unsigned)threadIdx.x));
+  }
   __syncthreads();
 
   const int cid = blockIdx.x / C;
@@ -807,7 +984,7 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
   const TailOut out{a.recs, a.cap, a.counter, a.dump, a.proj, a.kappa_hi, a.lag_end};
 
   for (int64_t k = a.k0 + cid; k < a.k1; k += ncl) {
-    template_columns<F, S, NC, T, HALFZ, true>(rank, a.bank + k * a.Lp, nz, nfold, a.AB);
+    template_columns<F, S, NC, T, HALFZ, true, IL>(rank, a.bank + k * a.Lp, nz, nfold, a.AB);
     cluster.sync();  // every column and every sigma partial of the cluster is ready
     float sigma;
     {  // Eq. PT over the cluster's partials, summed in rank order as group_sigma does
@@ -819,8 +996,8 @@ __global__ void __launch_bounds__(T, MINB) correlate_kernel(PlanDev p, Correlate
     const int64_t krow = k - a.k0;
     if (rank == 0 && threadIdx.x == 0) a.sigma[krow] = sigma;
     // S6: S-point combine, threshold, warp-ballot compaction
-    combine_and_emit<F, S, NC, T, EXT>(Smem<F, NC>::colptr(), H, rank, a.kappa * sigma,
-                                       (uint32_t)k, krow, out, sigma);
+    combine_and_emit<F, S, NC, T, EXT, IL>(Smem<F, NC>::colptr(), H, rank, a.kappa * sigma,
+                                           (uint32_t)k, krow, out, sigma);
     cluster_sync_after_reads();  // remote reads done before the columns are overwritten
   }
 }
@@ -837,7 +1014,11 @@ template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool EXT>
 static cudaError_t launch_corr_tp(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
   constexpr int C = ColMap<S, NC>::C;
   constexpr size_t smem = Lay<F, NC>::total;
-  auto kern = correlate_kernel<F, S, NC, T, MINB, HALFZ, EXT>;
+  // interleaved columns for S = 16 (N = 2^17), where the 16-column combine
+  // halves its remote loads: 31.6 against 33.1 ms per 65536 templates; for
+  // S <= 8 they measured level or slower (the one-round passes spill)
+  constexpr bool kIL = (F == 4096 && S == 16 && NC == 2 && T == 256 && HALFZ);
+  auto kern = correlate_kernel<F, S, NC, T, MINB, HALFZ, EXT, kIL>;
   cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

@@ -339,8 +339,13 @@ def test_invalid_arguments(ctx):
     bid2 = ctx.bege_define_bank_samples(np.ones((2, 16), np.float32))
     with pytest.raises(BegeError):
         ctx.bege_correlate(seg, bid2, 0, 3, 5.0)                 # range outside bank
+    with pytest.raises(BegeError) as e:
+        ctx.bege_correlate(seg, bid2, 1, 1, 5.0)                 # empty range
+    assert e.value.code == -1
     with pytest.raises(BegeError):
         ctx.bege_correlate(seg, bid2, 0, 2, float("nan"))
+    with pytest.raises(BegeError):
+        ctx.bege_correlate(seg, bid2, 0, 2, float("inf"))
     with pytest.raises(BegeError):
         ctx.bege_correlate(seg, 999999, 0, 1, 5.0)               # unknown handle
     with pytest.raises(BegeError):
