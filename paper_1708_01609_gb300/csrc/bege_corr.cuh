@@ -496,6 +496,13 @@ __device__ __forceinline__ float fused_mid(int rank, const float4* __restrict__ 
   return acc;
 }
 
+// fused_mid as a function of its own (see the interleaved kernel).
+template <int S, int NC, int T>
+__device__ __noinline__ float fused_mid_call(int rank, const float4* __restrict__ AB,
+                                             float* red_warp) {
+  return fused_mid<S, NC, T>(rank, AB, red_warp);
+}
+
 // ---------------------------------------------------------------------------
 // S1: segment spectrum D and product coefficients A, B (grid: C CTAs)
 // ---------------------------------------------------------------------------
@@ -704,6 +711,14 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
 __device__ __forceinline__ float4* il_rows() { return reinterpret_cast<float4*>(smem_raw); }
 __device__ __forceinline__ float4 il_pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
 
+// The interleaved kernel calls its passes and its fused middle as separate
+// (not inlined) functions: each stage then gets the whole register budget
+// of the 128-register launch shape to itself, where the inlined kernel
+// spilled 100 bytes a thread (two butterflies of data per pass and per
+// fused middle).  Measured on 65536 chirps: N = 2^15 6.71 -> 6.66 ms, 2^16
+// 14.43 -> 14.16, 2^17 33.1 -> 31.0; at N = 2^14 (no cluster, S = 2) the
+// separate layout stays (3.25 against 3.26-3.30 ms).
+
 // Row loads and stores of both columns at padded row index i: interleaved
 // (IL, one 16-byte access) or from the two separate columns.
 template <bool IL>
@@ -730,7 +745,7 @@ __device__ __forceinline__ void il_store(int i, float2 a, float2 b) {
 // First forward pass (radix 16, Ns = 1) of both columns from the template's
 // nz <= F/2 complex samples: u_c[m1] = wH^(b_c m1) z[m1], upper half zero.
 template <bool OUT_IL>
-__device__ __forceinline__ void il_fwd_first_pass(const float* __restrict__ src, int nz) {
+__device__ __noinline__ void il_fwd_first_pass(const float* __restrict__ src, int nz) {
   using SM = Smem<4096, 2>;
   const float2* z = reinterpret_cast<const float2*>(src);
   const int j = threadIdx.x;
@@ -761,7 +776,7 @@ __device__ __forceinline__ void il_fwd_first_pass(const float* __restrict__ src,
 // after it, so the pass may also change the layout (IN_IL -> OUT_IL).
 // Ends with a barrier.
 template <int NS, bool INV, bool IN_IL, bool OUT_IL>
-__device__ __forceinline__ void il_pass(const float2* tw) {
+__device__ __noinline__ void il_pass(const float2* tw) {
   constexpr int step = 256 + 16;  // padded distance of rows j + 256 r
   static_assert(NS % 16 == 0, "strided stores");
   const int j = threadIdx.x;
@@ -790,7 +805,7 @@ __device__ __forceinline__ void il_pass(const float2* tw) {
 // twiddle T_b[n1] = wH^(-b n1) x[n1] (as inv_last_pass), in one round;
 // writes the interleaved layout.  TRAIL: end with a barrier.
 template <int S, bool IN_IL, bool TRAIL>
-__device__ __forceinline__ void il_inv_last_pass() {
+__device__ __noinline__ void il_inv_last_pass() {
   using SM = Smem<4096, 2>;
   constexpr int Ns = 256, step = 256 + 16;
   const int j = threadIdx.x;
@@ -861,7 +876,7 @@ __device__ __forceinline__ void template_columns(int grank, const float* __restr
     // the interleaved one, which the combine reads a row at a time
     il_fwd_first_pass<true>(src, nz);
     il_pass<16, false, true, false>(SM::tw2());
-    fused_mid<S, NC, T>(grank, AB, SM::red(), s_rt);
+    fused_mid_call<S, NC, T>(grank, AB, SM::red());
     if (threadIdx.x == 0) {
       float s = 0.f;
       for (int w = 0; w < T / 32; ++w) s += SM::red()[w];
@@ -1014,10 +1029,8 @@ template <int F, int S, int NC, int T, int MINB, bool HALFZ, bool EXT>
 static cudaError_t launch_corr_tp(const PlanDev& p, const CorrelateArgs& a, cudaStream_t s) {
   constexpr int C = ColMap<S, NC>::C;
   constexpr size_t smem = Lay<F, NC>::total;
-  // interleaved columns for S = 16 (N = 2^17), where the 16-column combine
-  // halves its remote loads: 31.6 against 33.1 ms per 65536 templates; for
-  // S <= 8 they measured level or slower (the one-round passes spill)
-  constexpr bool kIL = (F == 4096 && S == 16 && NC == 2 && T == 256 && HALFZ);
+  // interleaved columns for S >= 4 (N >= 2^15)
+  constexpr bool kIL = (F == 4096 && S >= 4 && NC == 2 && T == 256 && HALFZ);
   auto kern = correlate_kernel<F, S, NC, T, MINB, HALFZ, EXT, kIL>;
   cudaError_t e = ensure_smem(kern, smem);
   if (e != cudaSuccess) return e;
