@@ -159,6 +159,19 @@ def _oracle_worker(args):
     return done, time.perf_counter() - t0
 
 
+def oracle_parity_case_rate() -> dict:
+    """The oracle on the N = 2^14 parity case (64 chirps, kappa 5), one
+    process: the small configuration beside the benchmark's."""
+    import oracle as O
+    seg, params = S.small_case()
+    t0 = time.perf_counter()
+    bank = O.chirp_bank(params, 4096.0, 4096, 0.05)
+    O.search(seg.y, bank, 5.0, batch=8)
+    dt = time.perf_counter() - t0
+    return {"value": len(params) / dt, "unit": UNIT, "cores": 1,
+            "sample": f"N=2^14 segment x 64 chirps (8 f0 x 8 fdot), one process, {dt:.2f} s"}
+
+
 def cpu_model() -> str:
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -191,7 +204,8 @@ def cpu_baseline(seconds: float = 15.0) -> dict:
                        f"{cores} processes, one per core, on disjoint slices of the 2^20 bank "
                        f"({total} templates, ~{seconds / 2:.0f} s each)"),
             "single_process": {"value": single, "cores": 1,
-                               "sample": f"the first {done} templates, {dt:.1f} s"}}
+                               "sample": f"the first {done} templates, {dt:.1f} s"},
+            "parity_case": oracle_parity_case_rate()}
 
 
 # ---------------------------------------------------------------------------
