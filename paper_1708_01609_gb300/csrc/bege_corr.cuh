@@ -708,8 +708,6 @@ __device__ __forceinline__ void combine_and_emit(float2* const* colptr, int H, i
 // in the same order as in the separate layout, and the fused middle keeps
 // its thread-to-item map, so the results are bitwise the same.
 // ---------------------------------------------------------------------------
-static_assert(Lay<4096, 2>::cols == 0 && Lay<4096, 2>::tw3 >= size_t(Lay<4096, 2>::CS) * 16,
-              "the interleaved rows occupy the two columns' bytes at the start of shared memory");
 __device__ __forceinline__ float4* il_rows() { return reinterpret_cast<float4*>(smem_raw); }
 __device__ __forceinline__ float4 il_pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
 
