@@ -32,11 +32,8 @@ def deal(pending: list, alive: list[int]) -> dict:
     """Deal the pending chunks (in row order) to the live ranks as
     contiguous runs whose lengths differ by at most one, so that in the
     first round each rank gets one contiguous range of the bank."""
-    out, i = {}, 0
-    for r, (a, b) in zip(alive, shard_ranges(len(pending), len(alive))):
-        out[r] = pending[a:b]
-        i = b
-    return out
+    return {r: pending[a:b]
+            for r, (a, b) in zip(alive, shard_ranges(len(pending), len(alive)))}
 
 
 def first_range(count: int, chunk: int, world: int, rank: int) -> tuple[int, int]:
@@ -112,8 +109,9 @@ def run_sharded(dist, compute, count: int, chunk: int, fail_rank: int | None = N
     ``compute(k0, k1)`` returns this rank's tail records for rows [k0, k1),
     or a pair (records, (snr, tmpl)) with the chunk's per-lag maximum
     (Eq. Ak over those rows, as bege_fetch_max returns it).  Chunks are
-    dealt as contiguous runs (``deal``); after every round the ranks exchange (on the host,
-    via all_gather_object) which chunks they finished.  A rank that raises
+    dealt as contiguous runs (``deal``); after every round the ranks
+    exchange (on the host, via all_gather_object) which chunks they
+    finished.  A rank that raises
     is treated as failed: it reports no more progress, and its unfinished
     chunks are dealt again to the survivors.  ``fail_rank`` / ``fail_after``
     make that rank fail after that many chunks (fault injection for tests).
