@@ -114,12 +114,23 @@ def test_fetch_max_rejects_plain_jobs_and_wrong_length():
     ctx.close()
 
 
+def band_case(n):
+    """The 64-chirp parity bank against a segment of n samples with one
+    20-sigma injection of template 27: the N = 2^14 parity case itself, or
+    N = 2^16 (the clustered, interleaved-column kernel)."""
+    if n == 1 << 14:
+        return S.small_case()
+    params = S.grid_small()
+    return S.make_segment(n, params, 1, 1234, fixed=[(27, 20000, 20.0)]), params
+
+
+@pytest.mark.parametrize("n_seg", [1 << 14, 1 << 16], ids=["N16384", "N65536"])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
-def test_band_tails_match_oracle(prec):
+def test_band_tails_match_oracle(prec, n_seg):
     """Tails over a finite band (Sec. 5): kappa_lo sigma < |rho| < kappa_hi
-    sigma on the N = 2^14 case, against the oracle; entries within the
+    sigma on the parity bank (N = 2^14 and 2^16), against the oracle; entries within the
     tolerance band of either end are excluded from set parity."""
-    seg_data, params = S.small_case()
+    seg_data, params = band_case(n_seg)
     lo, hi = 3.5, 4.25
     ctx = make_ctx(tail_capacity=1 << 20, precision=prec)
     seg = ctx.bege_load_segment(seg_data.y)
@@ -146,15 +157,16 @@ def test_band_tails_match_oracle(prec):
     for (k, n), v in got.items():
         a = abs(rho[k][n]) / sig[k]
         assert lo - near <= a <= hi + near, (k, n, a)
-    assert n_ref > 300  # ~470 expected from noise alone, plus the injection
+    assert n_ref > 300  # from noise alone ~470 at N = 2^14 (four times that at 2^16), plus the injection
 
 
+@pytest.mark.parametrize("n_seg", [1 << 14, 1 << 16], ids=["N16384", "N65536"])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
-def test_linear_tails_match_oracle(prec):
+def test_linear_tails_match_oracle(prec, n_seg):
     """Overlap-save mask: tails only at lags n <= N - L (the windows that do
-    not wrap), on the N = 2^14 case against the oracle's tails_linear; sigma
+    not wrap), on the parity bank (N = 2^14 and 2^16) against the oracle's tails_linear; sigma
     is the full Parseval value."""
-    seg_data, params = S.small_case()
+    seg_data, params = band_case(n_seg)
     kappa, length, n = 4.0, 4096, len(seg_data.y)
     ctx = make_ctx(tail_capacity=1 << 20, precision=prec)
     seg = ctx.bege_load_segment(seg_data.y)
@@ -190,12 +202,13 @@ def test_linear_tails_match_oracle(prec):
     assert n_ref > 100
 
 
+@pytest.mark.parametrize("n_seg", [1 << 14, 1 << 16], ids=["N16384", "N65536"])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
-def test_ex_options_compose(prec):
+def test_ex_options_compose(prec, n_seg):
     """bege_correlate_ex with band, mask and projection together: the
     records are the plain search's records filtered by both rules, and the
     projection is the per-lag maximum of those records."""
-    seg_data, params = S.small_case()
+    seg_data, params = band_case(n_seg)
     lo, hi, length, n = 3.5, 6.0, 4096, len(seg_data.y)
     ctx = make_ctx(tail_capacity=1 << 20, precision=prec)
     seg = ctx.bege_load_segment(seg_data.y)
