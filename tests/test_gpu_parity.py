@@ -127,12 +127,14 @@ def test_symmetric_chirp_bank_matches_oracle(ctx):
         ctx.bege_release(bid)
 
 
-def test_symmetric_bank_finds_a_descending_chirp(ctx):
-    """N = 2^14 noise with a time-reversed (descending) chirp injected at lag
-    5000: the symmetric bank's tails match the oracle's and contain the
-    injection at its template, which the plain bank misses."""
+@pytest.mark.parametrize("n", [1 << 14, 1 << 17])
+def test_symmetric_bank_finds_a_descending_chirp(ctx, n):
+    """Noise (N = 2^14, and 2^17 for the interleaved-column kernel with 16
+    columns) with a time-reversed (descending) chirp injected at lag 5000:
+    the symmetric bank's tails match the oracle's and contain the injection
+    at its template, which the plain bank misses."""
     params = S.grid_small()
-    n, lag, k = 1 << 14, 5000, 27
+    lag, k = 5000, 27
     f0, fd = params[k]
     y = S.band_limited_noise(n, 77).astype(np.float64)
     down = S.chirp_signal(f0, fd, 4096)[::-1]

@@ -11,6 +11,16 @@ from gpu_helpers import make_ctx, oracle_rho
 pytestmark = pytest.mark.gpu
 
 
+def band_case(n):
+    """The 64-chirp parity bank against a segment of n samples with one
+    20-sigma injection of template 27: the N = 2^14 parity case itself, or
+    N = 2^16 (the clustered, interleaved-column kernel)."""
+    if n == 1 << 14:
+        return S.small_case()
+    params = S.grid_small()
+    return S.make_segment(n, params, 1, 1234, fixed=[(27, 20000, 20.0)]), params
+
+
 def projection_of_records(recs, sigma, kappa, n, k0=0):
     """The kernel's rule on its own records: v > fl(kappa sigma), key
     fl(v (1 / sigma)), ties to the smaller template; in FP32."""
@@ -32,9 +42,10 @@ def projection_of_records(recs, sigma, kappa, n, k0=0):
     return out_snr, out_k
 
 
+@pytest.mark.parametrize("n_seg", [1 << 14, 1 << 16], ids=["N16384", "N65536"])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
-def test_projection_matches_oracle(prec):
-    seg_data, params = S.small_case()
+def test_projection_matches_oracle(prec, n_seg):
+    seg_data, params = band_case(n_seg)
     kappa = 4.0
     ctx = make_ctx(tail_capacity=1 << 20, precision=prec)
     seg = ctx.bege_load_segment(seg_data.y)
@@ -113,15 +124,6 @@ def test_fetch_max_rejects_plain_jobs_and_wrong_length():
         ctx.bege_fetch_max(job, len(seg_data.y) // 2)
     ctx.close()
 
-
-def band_case(n):
-    """The 64-chirp parity bank against a segment of n samples with one
-    20-sigma injection of template 27: the N = 2^14 parity case itself, or
-    N = 2^16 (the clustered, interleaved-column kernel)."""
-    if n == 1 << 14:
-        return S.small_case()
-    params = S.grid_small()
-    return S.make_segment(n, params, 1, 1234, fixed=[(27, 20000, 20.0)]), params
 
 
 @pytest.mark.parametrize("n_seg", [1 << 14, 1 << 16], ids=["N16384", "N65536"])
